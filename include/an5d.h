@@ -1,0 +1,209 @@
+/*
+ * an5d.h -- C ABI of a GB300 (sm_103a) library for iterated star/box
+ * Jacobi stencil sweeps with high-degree N.5D temporal blocking.
+ *
+ * Method: AN5D (Matsumura, Zohouri, Wahib, Endo, Matsuoka, CGO 2020).
+ *   - Stencils (Section 2.1, Table 4): star (axis neighbours only) or box
+ *     (full (2R+1)^d cube) of radius R, constant per-offset coefficients,
+ *     one array, one statement, on 2D or 3D grids.
+ *   - N.5D blocking (Section 2.3, Fig. 1; Section 3.1): tile all axes but the
+ *     slowest one, stream along it, and fuse bT time steps per pass over
+ *     global memory with overlapped halo tiles (2 * bT * R per tiled axis).
+ *   - Host code (Section 3.3): one kernel pass per bT steps, a final pass
+ *     with a reduced degree when T is not a multiple of bT, buffers swapped
+ *     so that the result lands in the caller's output.
+ *
+ * Data layout (all entry points): a grid with interior extents dims[]
+ * (C order, slowest first, x = last axis contiguous) is stored as a dense
+ * padded array of (dims[i] + 2R) elements per axis, C order, no row pitch.
+ * The R-wide halo holds fixed (Dirichlet) boundary values: it is read,
+ * never updated.  Device pointers must be 16-byte aligned.
+ *
+ * Per-point update, for every interior point p (coefficient k multiplies
+ * offset o_k in the canonical order below):
+ *     acc = c[0] * u[p + o_0];  acc = fma(c[k], u[p + o_k], acc), k = 1..n-1
+ * in the run's precision, each operation rounded once.  Canonical order
+ * (Table 4's sums; box streaming axis outermost as in the per-sub-plane
+ * partial sums of Section 3.1):
+ *     star: centre, then for i = -R..-1, 1..R: (dx=i), (dy=i)[, (dz=i)]
+ *     box : for dz = -R..R (3D), dy = -R..R, dx = -R..R
+ * The plain FP32 and FP64 methods are bit-exact to this definition.
+ *
+ * Errors: functions returning int return an AN5D_* status (0 = success).
+ * Functions returning a pointer return NULL on failure.  The reason of the
+ * last failure on the calling thread is available from an5d_last_error()
+ * and an5d_last_status().  Device-side failures (a bounded wait that gave
+ * up) are recorded in the plan and read by an5d_plan_status() after the
+ * work has finished.  No entry point aborts the process.
+ *
+ * Ownership: a plan owns its device coefficient copy, its scratch buffers
+ * and its tuned configuration.  The caller owns every in/out buffer and
+ * every stream.  All device work is enqueued on the caller's stream
+ * (a cudaStream_t passed as void*; NULL = the legacy default stream) and
+ * is asynchronous unless stated.
+ */
+#ifndef AN5D_H
+#define AN5D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct an5d_plan an5d_plan;
+
+/* Stencil shape (Section 2.1). */
+typedef enum { AN5D_STAR = 0, AN5D_BOX = 1 } an5d_shape;
+
+/* Arithmetic of a run.
+ *   AN5D_F32             FP32 storage and FP32 plain chain (bit-exact).
+ *   AN5D_F64             FP64 storage and FP64 plain chain (bit-exact).
+ *   AN5D_F16S_F32C       binary16 storage, FP32 chain, every time level
+ *                        rounded to binary16 (nearest-even).
+ *   AN5D_F32_COMPENSATED FP32 storage, per-point sum by Dot2 (Ogita, Rump,
+ *                        Oishi 2005, Algorithm 5.3) in the canonical order.
+ * The paper itself evaluates FP32 and FP64 with fast-math (Section 5.2);
+ * the last two forms have no counterpart in the paper. */
+typedef enum {
+    AN5D_F32 = 0,
+    AN5D_F64 = 1,
+    AN5D_F16S_F32C = 2,
+    AN5D_F32_COMPENSATED = 3
+} an5d_dtype;
+
+/* Status codes. */
+enum {
+    AN5D_OK = 0,
+    AN5D_ERR_INVALID_ARG = -1, /* NULL pointer, bad extent, T < 0, misaligned pointer */
+    AN5D_ERR_UNSUPPORTED = -2, /* ndim, shape, radius or dtype not built into the library */
+    AN5D_ERR_ALIAS = -3,       /* out overlaps in */
+    AN5D_ERR_CUDA = -4,        /* a CUDA runtime call failed (message in an5d_last_error) */
+    AN5D_ERR_OOM = -5,         /* device allocation failed */
+    AN5D_ERR_TIMEOUT = -6      /* a bounded device wait gave up (plan status) */
+};
+
+/* Chosen blocking of a plan (Section 3.1 / 3.2 parameters).
+ *   bT          time steps fused per pass
+ *   tile_x      tile extent along x in cells, overlap included (b_S1)
+ *   tile_y      3D: tile extent along y in cells, overlap included (b_S2); 2D: 1
+ *   stream_axis index of the streamed axis in dims[] (0 = slowest)
+ *   hsn         streamed cells per stream block (h_SN, Section 3.2)
+ *   warps_per_cta, ctas   launch shape of one pass
+ *   model_gcells      analytic roofline prediction, GCell-updates/s
+ *   measured_gcells   timed throughput of this config during tuning (0 if untimed) */
+typedef struct {
+    int bT;
+    int tile_x;
+    int tile_y;
+    int stream_axis;
+    int hsn;
+    int warps_per_cta;
+    int ctas;
+    int reserved;
+    double model_gcells;
+    double measured_gcells;
+} an5d_config;
+
+/* Number of coefficients of a stencil: star 2*ndim*R+1, box (2R+1)^ndim
+ * (Table 4).  Returns a negative AN5D_* status for unsupported input. */
+int an5d_coeff_count(int ndim, an5d_shape shape, int radius);
+
+/* Create a plan for one stencil on one grid size (Section 3.3 host code).
+ *   ndim    2 or 3
+ *   shape   AN5D_STAR or AN5D_BOX
+ *   radius  1..4 for star; 1..2 for 2D box; 1 for 3D box
+ *   coeffs  host array of an5d_coeff_count(...) doubles in canonical order,
+ *           rounded once to the run's compute precision here
+ *   dtype   see an5d_dtype
+ *   dims    host array of ndim interior extents (each >= 1), slowest first;
+ *           the padded array must have fewer than 2^31 elements
+ * Picks the blocking with the library's analytic model (no GPU timing; see
+ * an5d_plan_tune).  Allocates the plan's scratch buffer (one padded grid)
+ * on the current device.  Returns NULL on failure. */
+an5d_plan *an5d_plan_create(int ndim, an5d_shape shape, int radius, const double *coeffs,
+                            an5d_dtype dtype, const int64_t *dims);
+
+/* Advance T time steps: out = S^T(in).
+ *   in, out  device pointers to padded arrays of the storage type
+ *            (FP32: float, FP64: double, F16S: binary16, COMPENSATED: float);
+ *            in is never written; out must not overlap in (AN5D_ERR_ALIAS);
+ *            out's halo is set to in's halo
+ *   T        >= 0; T == 0 copies in to out
+ *   stream   cudaStream_t as void*
+ * Enqueues ceil(T / bT) passes plus a halo copy; returns after enqueueing.
+ * Not thread-safe per plan: one run of a plan at a time (its scratch
+ * buffer is shared by all runs). */
+int an5d_run(an5d_plan *plan, const void *in, void *out, int64_t T, void *stream);
+
+/* Same as an5d_run on HOST buffers (pageable or pinned): copies in to the
+ * plan's device staging buffers, runs, copies the result back into out,
+ * and synchronises the stream before returning.  Allocates the staging
+ * buffers on first use. */
+int an5d_run_host(an5d_plan *plan, const void *in_host, void *out_host, int64_t T,
+                  void *stream);
+
+/* Release the plan and its device memory.  NULL-safe.  Synchronises the
+ * device work the plan has enqueued first. */
+void an5d_plan_destroy(an5d_plan *plan);
+
+/* Copy the plan's current configuration into *cfg. */
+int an5d_plan_config(const an5d_plan *plan, an5d_config *cfg);
+
+/* Force a configuration (bT, hsn; 0 = keep the current value).  Other
+ * fields are derived.  Returns AN5D_ERR_UNSUPPORTED for a bT not built. */
+int an5d_plan_set_config(an5d_plan *plan, int bT, int hsn);
+
+/* Autotune (Section 5.3's "Tuned" procedure with this library's model):
+ * rank every built bT and stream-block length with the analytic model,
+ * time the top `topk` candidates on the plan's scratch buffers for
+ * `T_probe` steps on `stream`, keep the fastest.  Synchronous.  Results
+ * are cached per (stencil, dtype, dims, device) for the process. */
+int an5d_plan_tune(an5d_plan *plan, int topk, int64_t T_probe, void *stream);
+
+/* Device-side status of the plan's finished work: AN5D_OK or
+ * AN5D_ERR_TIMEOUT.  Synchronises the device.  Clears the status. */
+int an5d_plan_status(an5d_plan *plan);
+
+/* Peak rates used by the library's analytic model and by roofline reports.
+ *   hbm_gbs      device copy bandwidth, read + write bytes, GB/s
+ *   fp32_gflops  FP32 fma throughput, 2 flops per fma, GFLOP/s
+ *   fp64_gflops  FP64 fma throughput, GFLOP/s
+ *   smem_gbs     shared-memory load bandwidth, GB/s
+ *   sm_clock_mhz peak SM clock of the device attribute (nominal figures)
+ *   sms          streaming multiprocessors
+ *   measured     1 if the figures come from an5d_measure_peaks, 0 if nominal
+ * The paper measures its memory peaks with micro-benchmarks and takes the
+ * compute peak from the FMA rate (Section 4); so does this library. */
+typedef struct {
+    double hbm_gbs;
+    double fp32_gflops;
+    double fp64_gflops;
+    double smem_gbs;
+    double sm_clock_mhz;
+    int sms;
+    int measured;
+} an5d_peaks;
+
+/* Run the copy (2 x 1 GiB), FP32 fma, FP64 fma and shared-memory load
+ * micro-benchmarks on the current device and `stream`, store the result as
+ * the model's peaks for this device and copy it to *out (may be NULL).
+ * Synchronous; allocates and frees 2 GiB of device memory. */
+int an5d_measure_peaks(an5d_peaks *out, void *stream);
+
+/* Current peaks of the current device: measured if an5d_measure_peaks ran
+ * in this process, else nominal figures from the device attributes. */
+int an5d_get_peaks(an5d_peaks *out);
+
+/* Message and status of the last failure on the calling thread. */
+const char *an5d_last_error(void);
+int an5d_last_status(void);
+
+/* Library version string. */
+const char *an5d_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AN5D_H */

@@ -1,0 +1,250 @@
+"""Python binding of the C ABI in include/an5d.h (ctypes; argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Torch
+tensors are passed as device pointers (``tensor.data_ptr()``) and streams
+as ``torch.cuda.Stream.cuda_stream``; no computation happens in Python.
+The library is the in-tree ``_build/liban5d.so``: if it is missing this
+module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .inputs import STAR, BOX  # noqa: F401  (re-exported shape codes)
+
+F32, F64, F16S_F32C, F32_COMPENSATED = 0, 1, 2, 3
+DTYPES = {"f32": F32, "f64": F64, "f16": F16S_F32C, "f32c": F32_COMPENSATED}
+
+AN5D_OK = 0
+AN5D_ERR_INVALID_ARG = -1
+AN5D_ERR_UNSUPPORTED = -2
+AN5D_ERR_ALIAS = -3
+AN5D_ERR_CUDA = -4
+AN5D_ERR_OOM = -5
+AN5D_ERR_TIMEOUT = -6
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liban5d.so")
+
+_lib = None
+
+
+class An5dError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"an5d status {status}: {msg}")
+        self.status = status
+
+
+class an5d_config(ctypes.Structure):
+    _fields_ = [("bT", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("stream_axis", ctypes.c_int), ("hsn", ctypes.c_int),
+                ("warps_per_cta", ctypes.c_int), ("ctas", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("model_gcells", ctypes.c_double),
+                ("measured_gcells", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class an5d_peaks(ctypes.Structure):
+    _fields_ = [("hbm_gbs", ctypes.c_double), ("fp32_gflops", ctypes.c_double),
+                ("fp64_gflops", ctypes.c_double), ("smem_gbs", ctypes.c_double),
+                ("sm_clock_mhz", ctypes.c_double), ("sms", ctypes.c_int),
+                ("measured", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def load(path: str = LIB_PATH):
+    """Load liban5d.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build the CUDA extension first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    L.an5d_coeff_count.argtypes = [I, I, I]
+    L.an5d_coeff_count.restype = I
+    L.an5d_plan_create.argtypes = [I, I, I, P, I, P]
+    L.an5d_plan_create.restype = P
+    L.an5d_run.argtypes = [P, P, P, I64, P]
+    L.an5d_run.restype = I
+    L.an5d_run_host.argtypes = [P, P, P, I64, P]
+    L.an5d_run_host.restype = I
+    L.an5d_plan_destroy.argtypes = [P]
+    L.an5d_plan_destroy.restype = None
+    L.an5d_plan_config.argtypes = [P, ctypes.POINTER(an5d_config)]
+    L.an5d_plan_config.restype = I
+    L.an5d_plan_set_config.argtypes = [P, I, I]
+    L.an5d_plan_set_config.restype = I
+    L.an5d_plan_tune.argtypes = [P, I, I64, P]
+    L.an5d_plan_tune.restype = I
+    L.an5d_plan_status.argtypes = [P]
+    L.an5d_plan_status.restype = I
+    L.an5d_measure_peaks.argtypes = [ctypes.POINTER(an5d_peaks), P]
+    L.an5d_measure_peaks.restype = I
+    L.an5d_get_peaks.argtypes = [ctypes.POINTER(an5d_peaks)]
+    L.an5d_get_peaks.restype = I
+    L.an5d_last_error.argtypes = []
+    L.an5d_last_error.restype = ctypes.c_char_p
+    L.an5d_last_status.argtypes = []
+    L.an5d_last_status.restype = I
+    L.an5d_version.argtypes = []
+    L.an5d_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int) -> int:
+    if rc != AN5D_OK:
+        raise An5dError(rc, an5d_last_error())
+    return rc
+
+
+def _ptr(x) -> int | None:
+    """Device or host address of a torch tensor, numpy array or int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# C entry points, same names.
+
+def an5d_version() -> str:
+    return load().an5d_version().decode()
+
+
+def an5d_last_error() -> str:
+    return load().an5d_last_error().decode()
+
+
+def an5d_last_status() -> int:
+    return load().an5d_last_status()
+
+
+def an5d_coeff_count(ndim: int, shape: int, radius: int) -> int:
+    n = load().an5d_coeff_count(ndim, shape, radius)
+    if n < 0:
+        raise An5dError(n, an5d_last_error())
+    return n
+
+
+def an5d_plan_create(ndim: int, shape: int, radius: int, coeffs, dtype, dims) -> int:
+    """Returns an opaque plan handle (int)."""
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int64))
+    h = load().an5d_plan_create(ndim, shape, radius, c.ctypes.data, dt, d.ctypes.data)
+    if not h:
+        raise An5dError(an5d_last_status(), an5d_last_error())
+    return h
+
+
+def an5d_run(plan: int, inp, out, T: int, stream=None) -> int:
+    return _check(load().an5d_run(plan, _ptr(inp), _ptr(out), int(T), _stream(stream)))
+
+
+def an5d_run_host(plan: int, inp: np.ndarray, out: np.ndarray, T: int, stream=None) -> int:
+    return _check(load().an5d_run_host(plan, _ptr(inp), _ptr(out), int(T), _stream(stream)))
+
+
+def an5d_plan_destroy(plan: int) -> None:
+    load().an5d_plan_destroy(plan)
+
+
+def an5d_plan_config(plan: int) -> dict:
+    cfg = an5d_config()
+    _check(load().an5d_plan_config(plan, ctypes.byref(cfg)))
+    return cfg.as_dict()
+
+
+def an5d_plan_set_config(plan: int, bT: int = 0, hsn: int = 0) -> int:
+    return _check(load().an5d_plan_set_config(plan, int(bT), int(hsn)))
+
+
+def an5d_plan_tune(plan: int, topk: int = 5, T_probe: int = 20, stream=None) -> int:
+    return _check(load().an5d_plan_tune(plan, int(topk), int(T_probe), _stream(stream)))
+
+
+def an5d_plan_status(plan: int) -> int:
+    return load().an5d_plan_status(plan)
+
+
+def an5d_measure_peaks(stream=None) -> dict:
+    pk = an5d_peaks()
+    _check(load().an5d_measure_peaks(ctypes.byref(pk), _stream(stream)))
+    return pk.as_dict()
+
+
+def an5d_get_peaks() -> dict:
+    pk = an5d_peaks()
+    _check(load().an5d_get_peaks(ctypes.byref(pk)))
+    return pk.as_dict()
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper.
+
+class Plan:
+    """RAII wrapper of an an5d plan."""
+
+    def __init__(self, ndim: int, shape: int, radius: int, coeffs, dtype, dims):
+        self.ndim, self.shape, self.radius = ndim, shape, radius
+        self.dtype = dtype
+        self.dims = tuple(int(d) for d in dims)
+        self.handle = an5d_plan_create(ndim, shape, radius, coeffs, dtype, dims)
+
+    def run(self, inp, out, T: int, stream=None) -> None:
+        an5d_run(self.handle, inp, out, T, stream)
+
+    def run_host(self, inp: np.ndarray, out: np.ndarray, T: int, stream=None) -> None:
+        an5d_run_host(self.handle, inp, out, T, stream)
+
+    def config(self) -> dict:
+        return an5d_plan_config(self.handle)
+
+    def set_config(self, bT: int = 0, hsn: int = 0) -> None:
+        an5d_plan_set_config(self.handle, bT, hsn)
+
+    def tune(self, topk: int = 5, T_probe: int = 20, stream=None) -> dict:
+        an5d_plan_tune(self.handle, topk, T_probe, stream)
+        return self.config()
+
+    def status(self) -> int:
+        return an5d_plan_status(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            an5d_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

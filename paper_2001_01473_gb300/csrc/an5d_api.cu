@@ -1,0 +1,642 @@
+// an5d_api.cu -- the C ABI declared in include/an5d.h: plans, the pass loop
+// of the host code (AN5D Section 3.3), the analytic model and the autotuner.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "an5d.h"
+#include "an5d_internal.h"
+#include "model.h"
+
+namespace an5d {
+
+std::vector<KernelEntry> &registry()
+{
+    static std::vector<KernelEntry> r;
+    return r;
+}
+
+const KernelEntry *find_kernel(const KernelKey &k)
+{
+    for (const auto &e : registry())
+        if (e.key == k) return &e;
+    return nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// Thread-local error reporting.
+
+static thread_local std::string g_err = "";
+static thread_local int g_status = AN5D_OK;
+
+static int fail(int status, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    g_status = status;
+    return status;
+}
+
+static int ok()
+{
+    g_status = AN5D_OK;
+    return AN5D_OK;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? AN5D_ERR_OOM : AN5D_ERR_CUDA,     \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Tensor-map encoding through the driver entry point (no -lcuda needed).
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+static size_t elem_size(int dtype)
+{
+    switch (dtype) {
+    case DT_F64: return 8;
+    case DT_F16S: return 2;
+    default: return 4;
+    }
+}
+
+// 1D tiled map over a whole padded array; box = tile + alignment slack.
+static int encode_row_map(CUtensorMap *m, const void *base, int dtype, int64_t total, int box)
+{
+    auto fn = encode_fn();
+    if (!fn) return fail(AN5D_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    CUtensorMapDataType t = dtype == DT_F64    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                            : dtype == DT_F16S ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    cuuint64_t dim[1] = {(cuuint64_t)total};
+    cuuint32_t boxd[1] = {(cuuint32_t)box};
+    cuuint32_t es[1] = {1};
+    CUresult r = fn(m, t, 1, const_cast<void *>(base), dim, nullptr, boxd, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(AN5D_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return AN5D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Halo copy: dst's halo := src's halo (one CTA per padded x row).
+
+template <typename W>
+__global__ void halo_copy_kernel(const W *__restrict__ src, W *__restrict__ dst, int nzp, int nyp,
+                                 int nxp, int hz, int R)
+{
+    const int row = blockIdx.x;
+    const int z = row / nyp, y = row % nyp;
+    const bool full = z < hz || z >= nzp - hz || y < R || y >= nyp - R;
+    const size_t base = (size_t)row * nxp;
+    if (full) {
+        for (int x = threadIdx.x; x < nxp; x += blockDim.x) dst[base + x] = src[base + x];
+    } else {
+        for (int x = threadIdx.x; x < 2 * R; x += blockDim.x) {
+            const int xx = x < R ? x : nxp - 2 * R + x;
+            dst[base + xx] = src[base + xx];
+        }
+    }
+}
+
+}  // namespace an5d
+
+using namespace an5d;
+
+// ---------------------------------------------------------------------------
+// Plan.
+
+struct an5d_plan {
+    int ndim, shape, radius, dtype;
+    int64_t dims[3];      // interior extents, slowest first (ndim entries used)
+    int64_t nz, ny, nx;   // interior extents as 3D (nz = 1 in 2D)
+    int64_t total;        // padded elements
+    size_t bytes;         // padded bytes
+    int n;                // coefficients
+    double coeffs[MAX_COEFFS];  // rounded to the compute precision
+    int device;
+    int sms;
+    void *scratch = nullptr;
+    int *d_status = nullptr;
+    void *stage_in = nullptr, *stage_out = nullptr;
+    int bt = 1;
+    int hsn = 0;
+    double model_gcells = 0, measured_gcells = 0;
+    int bt_max = 0;
+};
+
+extern "C" const char *an5d_version(void) { return "an5d-gb300 0.1 (sm_103a)"; }
+extern "C" const char *an5d_last_error(void) { return g_err.c_str(); }
+extern "C" int an5d_last_status(void) { return g_status; }
+
+extern "C" int an5d_coeff_count(int ndim, an5d_shape shape, int radius)
+{
+    if (ndim != 2 && ndim != 3) return fail(AN5D_ERR_UNSUPPORTED, "ndim must be 2 or 3");
+    if (radius < 1 || radius > 4) return fail(AN5D_ERR_UNSUPPORTED, "radius must be in 1..4");
+    if (shape == AN5D_STAR) return 2 * ndim * radius + 1;
+    if (shape == AN5D_BOX) {
+        int n = 1;
+        for (int i = 0; i < ndim; ++i) n *= 2 * radius + 1;
+        return n;
+    }
+    return fail(AN5D_ERR_INVALID_ARG, "shape must be AN5D_STAR or AN5D_BOX");
+}
+
+static int largest_bt(const an5d_plan *p)
+{
+    int best = 0;
+    for (const auto &e : registry())
+        if (e.key.ndim == p->ndim && e.key.shape == p->shape && e.key.radius == p->radius &&
+            e.key.dtype == p->dtype)
+            best = std::max(best, e.key.bt);
+    return best;
+}
+
+// Geometry of one pass with degree bt.
+struct PassGeom {
+    const KernelEntry *k;
+    int tile_stride_x, tiles_x, tile_stride_y, tiles_y, hsn, stream_blocks, units, ctas;
+};
+
+static int pass_geometry(const an5d_plan *p, int bt, int hsn_req, PassGeom *g)
+{
+    g->k = find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt});
+    if (!g->k)
+        return fail(AN5D_ERR_UNSUPPORTED, "no kernel for ndim=%d shape=%d R=%d dtype=%d bT=%d",
+                    p->ndim, p->shape, p->radius, p->dtype, bt);
+    const int R = p->radius;
+    g->tile_stride_x = g->k->tile_x - 2 * bt * R;
+    g->tiles_x = (int)((p->nx + g->tile_stride_x - 1) / g->tile_stride_x);
+    if (p->ndim == 3) {
+        g->tile_stride_y = g->k->tile_y - 2 * bt * R;
+        g->tiles_y = (int)((p->ny + g->tile_stride_y - 1) / g->tile_stride_y);
+    } else {
+        g->tile_stride_y = 1;
+        g->tiles_y = 1;
+    }
+    const int64_t slen = p->ndim == 3 ? p->nz : p->ny;
+    int hsn = hsn_req > 0 ? hsn_req : (int)slen;
+    hsn = (int)std::min<int64_t>(std::max(1, hsn), slen);
+    g->hsn = hsn;
+    g->stream_blocks = (int)((slen + hsn - 1) / hsn);
+    const int64_t units = (int64_t)g->tiles_x * g->tiles_y * g->stream_blocks;
+    if (units > (1ll << 30)) return fail(AN5D_ERR_UNSUPPORTED, "grid too large");
+    g->units = (int)units;
+    g->ctas = (g->units + g->k->units_per_cta - 1) / g->k->units_per_cta;
+    return AN5D_OK;
+}
+
+// Resident work units per SM for a kernel (occupancy query).
+static int resident_units(const KernelEntry *k)
+{
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k->func, k->threads,
+                                                      k->smem_bytes) != cudaSuccess)
+        blocks = 1;
+    if (k->smem_bytes > 48 * 1024) {
+        // the attribute may not be set yet: estimate from shared memory alone
+        cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)k->smem_bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k->func, k->threads, k->smem_bytes);
+    }
+    return std::max(1, blocks) * k->units_per_cta;
+}
+
+// Stream-block length that makes the pass one (or `waves`) full wave(s).
+static int default_hsn(const an5d_plan *p, int bt, int waves)
+{
+    PassGeom g;
+    if (pass_geometry(p, bt, 0, &g)) return 0;
+    const int64_t cap = (int64_t)resident_units(g.k) * p->sms * waves;
+    const int64_t tiles = (int64_t)g.tiles_x * g.tiles_y;
+    const int64_t slen = p->ndim == 3 ? p->nz : p->ny;
+    int64_t nsb = std::max<int64_t>(1, cap / std::max<int64_t>(1, tiles));
+    nsb = std::min(nsb, slen);
+    return (int)((slen + nsb - 1) / nsb);
+}
+
+static double model_for(const an5d_plan *p, int bt, int hsn)
+{
+    PassGeom g;
+    if (pass_geometry(p, bt, hsn, &g)) return 0.0;
+    ModelInput mi;
+    mi.ndim = p->ndim;
+    mi.shape = p->shape;
+    mi.radius = p->radius;
+    mi.dtype = p->dtype;
+    mi.bt = bt;
+    mi.nz = p->nz;
+    mi.ny = p->ny;
+    mi.nx = p->nx;
+    mi.tile_x = g.k->tile_x;
+    mi.tile_y = g.k->tile_y;
+    mi.tiles_x = g.tiles_x;
+    mi.tiles_y = g.tiles_y;
+    mi.hsn = g.hsn;
+    mi.stream_blocks = g.stream_blocks;
+    mi.units = g.units;
+    mi.resident_units = resident_units(g.k) * p->sms;
+    mi.sms = p->sms;
+    return model_gcells(mi);
+}
+
+static void choose_default(an5d_plan *p)
+{
+    double best = -1.0;
+    int bbt = 1, bh = 0;
+    for (int bt = 1; bt <= p->bt_max; ++bt) {
+        if (!find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt})) continue;
+        const int h = default_hsn(p, bt, 1);
+        const double m = model_for(p, bt, h);
+        if (m > best) {
+            best = m;
+            bbt = bt;
+            bh = h;
+        }
+    }
+    p->bt = bbt;
+    p->hsn = bh;
+    p->model_gcells = best;
+    p->measured_gcells = 0.0;
+}
+
+extern "C" an5d_plan *an5d_plan_create(int ndim, an5d_shape shape, int radius,
+                                       const double *coeffs, an5d_dtype dtype,
+                                       const int64_t *dims)
+{
+    int n = an5d_coeff_count(ndim, shape, radius);
+    if (n < 0) return nullptr;
+    if (!coeffs || !dims) {
+        fail(AN5D_ERR_INVALID_ARG, "coeffs and dims must not be NULL");
+        return nullptr;
+    }
+    if (dtype < AN5D_F32 || dtype > AN5D_F32_COMPENSATED) {
+        fail(AN5D_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+        return nullptr;
+    }
+    int64_t total = 1;
+    for (int i = 0; i < ndim; ++i) {
+        if (dims[i] < 1 || dims[i] > (1ll << 30)) {
+            fail(AN5D_ERR_INVALID_ARG, "dims[%d] = %lld out of range", i, (long long)dims[i]);
+            return nullptr;
+        }
+        total *= dims[i] + 2 * radius;
+        if (total >= (1ll << 31)) {
+            fail(AN5D_ERR_UNSUPPORTED, "padded array must have fewer than 2^31 elements");
+            return nullptr;
+        }
+    }
+    an5d_plan *p = new an5d_plan();
+    p->ndim = ndim;
+    p->shape = shape;
+    p->radius = radius;
+    p->dtype = dtype;
+    p->n = n;
+    for (int i = 0; i < 3; ++i) p->dims[i] = i < ndim ? dims[i] : 0;
+    p->nz = ndim == 3 ? dims[0] : 1;
+    p->ny = dims[ndim - 2];
+    p->nx = dims[ndim - 1];
+    p->total = total;
+    p->bytes = (size_t)total * elem_size(dtype);
+    const bool dbl = dtype == AN5D_F64;
+    for (int k = 0; k < n; ++k) p->coeffs[k] = dbl ? coeffs[k] : (double)(float)coeffs[k];
+    p->bt_max = largest_bt(p);
+    if (p->bt_max == 0) {
+        fail(AN5D_ERR_UNSUPPORTED, "stencil ndim=%d shape=%d R=%d dtype=%d is not built", ndim,
+             (int)shape, radius, (int)dtype);
+        delete p;
+        return nullptr;
+    }
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&p->scratch, p->bytes);
+    if (e != cudaSuccess) {
+        fail(e == cudaErrorMemoryAllocation ? AN5D_ERR_OOM : AN5D_ERR_CUDA, "plan setup: %s",
+             cudaGetErrorString(e));
+        cudaFree(p->d_status);
+        cudaFree(p->scratch);
+        delete p;
+        return nullptr;
+    }
+    choose_default(p);
+    ok();
+    return p;
+}
+
+extern "C" void an5d_plan_destroy(an5d_plan *p)
+{
+    if (!p) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    cudaFree(p->scratch);
+    cudaFree(p->d_status);
+    cudaFree(p->stage_in);
+    cudaFree(p->stage_out);
+    if (cur >= 0) cudaSetDevice(cur);
+    delete p;
+}
+
+extern "C" int an5d_plan_config(const an5d_plan *p, an5d_config *cfg)
+{
+    if (!p || !cfg) return fail(AN5D_ERR_INVALID_ARG, "NULL plan or cfg");
+    PassGeom g;
+    if (int s = pass_geometry(p, p->bt, p->hsn, &g)) return s;
+    cfg->bT = p->bt;
+    cfg->tile_x = g.k->tile_x;
+    cfg->tile_y = g.k->tile_y;
+    cfg->stream_axis = 0;
+    cfg->hsn = g.hsn;
+    cfg->warps_per_cta = g.k->threads / 32;
+    cfg->ctas = g.ctas;
+    cfg->reserved = 0;
+    cfg->model_gcells = p->model_gcells;
+    cfg->measured_gcells = p->measured_gcells;
+    return ok();
+}
+
+extern "C" int an5d_plan_set_config(an5d_plan *p, int bt, int hsn)
+{
+    if (!p) return fail(AN5D_ERR_INVALID_ARG, "NULL plan");
+    if (bt < 0 || hsn < 0) return fail(AN5D_ERR_INVALID_ARG, "bT and hsn must be >= 0");
+    const int nbt = bt > 0 ? bt : p->bt;
+    if (!find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, nbt}))
+        return fail(AN5D_ERR_UNSUPPORTED, "bT=%d is not built for this stencil", nbt);
+    p->bt = nbt;
+    p->hsn = hsn > 0 ? hsn : default_hsn(p, nbt, 1);
+    p->model_gcells = model_for(p, p->bt, p->hsn);
+    p->measured_gcells = 0.0;
+    return ok();
+}
+
+static bool overlaps(const void *a, const void *b, size_t n)
+{
+    const char *x = (const char *)a, *y = (const char *)b;
+    return x < y + n && y < x + n;
+}
+
+static int launch_halo_copy(const an5d_plan *p, const void *src, void *dst, cudaStream_t st)
+{
+    const int R = p->radius;
+    const int hz = p->ndim == 3 ? R : 0;
+    const int nzp = (int)(p->nz + 2 * hz), nyp = (int)(p->ny + 2 * R), nxp = (int)(p->nx + 2 * R);
+    const int rows = nzp * nyp;
+    switch (elem_size(p->dtype)) {
+    case 2:
+        halo_copy_kernel<uint16_t><<<rows, 128, 0, st>>>((const uint16_t *)src, (uint16_t *)dst, nzp,
+                                                         nyp, nxp, hz, R);
+        break;
+    case 8:
+        halo_copy_kernel<uint64_t><<<rows, 128, 0, st>>>((const uint64_t *)src, (uint64_t *)dst, nzp,
+                                                         nyp, nxp, hz, R);
+        break;
+    default:
+        halo_copy_kernel<uint32_t><<<rows, 128, 0, st>>>((const uint32_t *)src, (uint32_t *)dst, nzp,
+                                                         nyp, nxp, hz, R);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return AN5D_OK;
+}
+
+static int launch_pass(const an5d_plan *p, int bt, const void *src, void *dst, cudaStream_t st)
+{
+    PassGeom g;
+    if (int s = pass_geometry(p, bt, p->hsn, &g)) return s;
+    PassDesc d;
+    memset(&d, 0, sizeof(d));
+    const int A = 16 / (int)elem_size(p->dtype);
+    if (int s = encode_row_map(&d.tmap, src, p->dtype, p->total, g.k->tile_x + A)) return s;
+    d.dst = dst;
+    d.status = p->d_status;
+    d.pitch = p->nx + 2 * p->radius;
+    d.plane = d.pitch * (p->ny + 2 * p->radius);
+    d.nz = (int)p->nz;
+    d.ny = (int)p->ny;
+    d.nx = (int)p->nx;
+    d.tile_stride_x = g.tile_stride_x;
+    d.tile_stride_y = g.tile_stride_y;
+    d.tiles_x = g.tiles_x;
+    d.tiles_y = g.tiles_y;
+    d.hsn = g.hsn;
+    d.stream_blocks = g.stream_blocks;
+    d.total_units = g.units;
+    d.ctas = g.ctas;
+    for (int k = 0; k < p->n; ++k) d.coeffs[k] = p->coeffs[k];
+    CUDA_TRY(g.k->launch(d, st));
+    return AN5D_OK;
+}
+
+static int run_impl(an5d_plan *p, const void *in, void *out, int64_t T, cudaStream_t st)
+{
+    if (T == 0) {
+        CUDA_TRY(cudaMemcpyAsync(out, in, p->bytes, cudaMemcpyDeviceToDevice, st));
+        return ok();
+    }
+    // Pass list (Section 3.3): floor(T/bT) passes of bT, then one of T mod bT.
+    std::vector<int> passes((size_t)(T / p->bt), p->bt);
+    if (T % p->bt) passes.push_back((int)(T % p->bt));
+    const size_t np = passes.size();
+    if (int s = launch_halo_copy(p, in, out, st)) return s;
+    if (np > 1)
+        if (int s = launch_halo_copy(p, in, p->scratch, st)) return s;
+    const void *src = in;
+    for (size_t k = 0; k < np; ++k) {
+        void *dst = ((np - 1 - k) % 2 == 0) ? out : p->scratch;
+        if (int s = launch_pass(p, passes[k], src, dst, st)) return s;
+        src = dst;
+    }
+    return ok();
+}
+
+static int check_run_args(an5d_plan *p, const void *in, const void *out, int64_t T)
+{
+    if (!p) return fail(AN5D_ERR_INVALID_ARG, "NULL plan");
+    if (!in || !out) return fail(AN5D_ERR_INVALID_ARG, "NULL in/out");
+    if (T < 0) return fail(AN5D_ERR_INVALID_ARG, "T must be >= 0");
+    if (((uintptr_t)in | (uintptr_t)out) & 15)
+        return fail(AN5D_ERR_INVALID_ARG, "in/out must be 16-byte aligned");
+    if (overlaps(in, out, p->bytes)) return fail(AN5D_ERR_ALIAS, "out overlaps in");
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != p->device)
+        return fail(AN5D_ERR_INVALID_ARG, "current device %d differs from the plan's device %d", dev,
+                    p->device);
+    return AN5D_OK;
+}
+
+extern "C" int an5d_run(an5d_plan *p, const void *in, void *out, int64_t T, void *stream)
+{
+    if (int s = check_run_args(p, in, out, T)) return s;
+    return run_impl(p, in, out, T, (cudaStream_t)stream);
+}
+
+extern "C" int an5d_run_host(an5d_plan *p, const void *in_host, void *out_host, int64_t T,
+                             void *stream)
+{
+    if (!p || !in_host || !out_host) return fail(AN5D_ERR_INVALID_ARG, "NULL argument");
+    if (T < 0) return fail(AN5D_ERR_INVALID_ARG, "T must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!p->stage_in) CUDA_TRY(cudaMalloc(&p->stage_in, p->bytes));
+    if (!p->stage_out) CUDA_TRY(cudaMalloc(&p->stage_out, p->bytes));
+    CUDA_TRY(cudaMemcpyAsync(p->stage_in, in_host, p->bytes, cudaMemcpyHostToDevice, st));
+    if (int s = run_impl(p, p->stage_in, p->stage_out, T, st)) return s;
+    CUDA_TRY(cudaMemcpyAsync(out_host, p->stage_out, p->bytes, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return ok();
+}
+
+extern "C" int an5d_plan_status(an5d_plan *p)
+{
+    if (!p) return fail(AN5D_ERR_INVALID_ARG, "NULL plan");
+    CUDA_TRY(cudaDeviceSynchronize());
+    int h = 0;
+    CUDA_TRY(cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(int)));
+    if (h & STATUS_TIMEOUT) return fail(AN5D_ERR_TIMEOUT, "a bounded device wait gave up");
+    return ok();
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner (Section 5.3 "Tuned": model-ranked candidates, top-k timed).
+
+namespace {
+struct TuneKey {
+    int ndim, shape, radius, dtype, device;
+    int64_t nz, ny, nx;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(ndim, shape, radius, dtype, device, nz, ny, nx) <
+               std::tie(o.ndim, o.shape, o.radius, o.dtype, o.device, o.nz, o.ny, o.nx);
+    }
+};
+struct TuneVal {
+    int bt, hsn;
+    double model, measured;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+}  // namespace
+
+extern "C" int an5d_plan_tune(an5d_plan *p, int topk, int64_t T_probe, void *stream)
+{
+    if (!p) return fail(AN5D_ERR_INVALID_ARG, "NULL plan");
+    if (topk < 1) topk = 1;
+    if (T_probe < 1) T_probe = 1;
+    TuneKey key{p->ndim, p->shape, p->radius, p->dtype, p->device, p->nz, p->ny, p->nx};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            p->bt = it->second.bt;
+            p->hsn = it->second.hsn;
+            p->model_gcells = it->second.model;
+            p->measured_gcells = it->second.measured;
+            return ok();
+        }
+    }
+    struct Cand {
+        int bt, hsn;
+        double model;
+    };
+    std::vector<Cand> cands;
+    for (int bt = 1; bt <= p->bt_max; ++bt) {
+        if (!find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt})) continue;
+        for (int waves = 1; waves <= 4; waves *= 2) {
+            const int h = default_hsn(p, bt, waves);
+            if (h <= 0) continue;
+            bool dup = false;
+            for (auto &c : cands) dup |= (c.bt == bt && c.hsn == h);
+            if (!dup) cands.push_back({bt, h, model_for(p, bt, h)});
+        }
+    }
+    std::sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) { return a.model > b.model; });
+    if ((int)cands.size() > topk) cands.resize(topk);
+    cudaStream_t st = (cudaStream_t)stream;
+    void *a = nullptr, *b = nullptr;
+    CUDA_TRY(cudaMalloc(&a, p->bytes));
+    cudaError_t e = cudaMalloc(&b, p->bytes);
+    if (e != cudaSuccess) {
+        cudaFree(a);
+        return fail(AN5D_ERR_OOM, "tune buffers: %s", cudaGetErrorString(e));
+    }
+    cudaMemsetAsync(a, 0, p->bytes, st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int save_bt = p->bt, save_hsn = p->hsn;
+    double best = -1.0;
+    Cand win = cands.empty() ? Cand{save_bt, save_hsn, 0.0} : cands[0];
+    int status = AN5D_OK;
+    for (const auto &c : cands) {
+        p->bt = c.bt;
+        p->hsn = c.hsn;
+        const int64_t T = std::max<int64_t>(T_probe, c.bt);
+        if ((status = run_impl(p, a, b, T, st))) break;   // warm-up
+        cudaEventRecord(e0, st);
+        if ((status = run_impl(p, a, b, T, st))) break;
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double g = (double)p->nz * p->ny * p->nx * T / (ms * 1e-3) / 1e9;
+        if (g > best) {
+            best = g;
+            win = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(a);
+    cudaFree(b);
+    if (status) {
+        p->bt = save_bt;
+        p->hsn = save_hsn;
+        return status;
+    }
+    p->bt = win.bt;
+    p->hsn = win.hsn;
+    p->model_gcells = win.model;
+    p->measured_gcells = best;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = TuneVal{win.bt, win.hsn, win.model, best};
+    }
+    return ok();
+}

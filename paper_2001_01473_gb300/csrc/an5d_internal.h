@@ -1,0 +1,75 @@
+// an5d_internal.h -- types shared by the C-ABI layer and the kernel
+// translation units: launch descriptors and the kernel registry.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace an5d {
+
+enum Dtype : int { DT_F32 = 0, DT_F64 = 1, DT_F16S = 2, DT_F32C = 3 };
+enum Shape : int { SH_STAR = 0, SH_BOX = 1 };
+
+constexpr int MAX_COEFFS = 128;
+
+// Bits of a plan's device status word.
+enum : int { STATUS_TIMEOUT = 1 };
+constexpr int WARPS_PER_CTA = 4;
+constexpr int CELLS_PER_LANE = 4;  // consecutive x cells owned by one lane
+constexpr int PREFETCH_ROWS = 3;   // TMA rows in flight ahead of the consumer
+
+// One pass of a streamed sweep (bT fused steps) over one grid.
+struct PassDesc {
+    CUtensorMap tmap;        // 1D tiled map over the whole padded source array
+    void *dst;               // padded destination array
+    int *status;             // device status word of the plan
+    int64_t pitch;           // elements per padded x row
+    int64_t plane;           // elements per padded xy plane (3D)
+    int nz, ny, nx;          // interior extents (nz = 1 in 2D)
+    int tile_stride_x;       // output columns per tile along x
+    int tile_stride_y;       // 3D: output rows per tile along y
+    int tiles_x, tiles_y;    // tiles per axis
+    int hsn;                 // output rows (2D) / planes (3D) per stream block
+    int stream_blocks;
+    int total_units;         // warps (2D) or CTAs (3D) that carry work
+    int ctas;                // grid size
+    double coeffs[MAX_COEFFS];
+};
+
+using LaunchFn = cudaError_t (*)(const PassDesc &, cudaStream_t);
+
+struct KernelKey {
+    int ndim, shape, radius, dtype, bt;
+    bool operator==(const KernelKey &o) const
+    {
+        return ndim == o.ndim && shape == o.shape && radius == o.radius && dtype == o.dtype &&
+               bt == o.bt;
+    }
+};
+
+struct KernelEntry {
+    KernelKey key;
+    LaunchFn launch;
+    const void *func;       // for cudaFuncGetAttributes / occupancy queries
+    int threads;            // threads per CTA
+    size_t smem_bytes;      // dynamic shared memory per CTA
+    int tile_x;             // tile width along x, overlap included
+    int tile_y;             // 3D tile height along y, overlap included (1 in 2D)
+    int units_per_cta;      // work units per CTA (warps in 2D, 1 in 3D)
+};
+
+std::vector<KernelEntry> &registry();
+
+struct Registrar {
+    Registrar(const KernelEntry *entries, int n)
+    {
+        for (int i = 0; i < n; ++i) registry().push_back(entries[i]);
+    }
+};
+
+const KernelEntry *find_kernel(const KernelKey &k);
+
+}  // namespace an5d

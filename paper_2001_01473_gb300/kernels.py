@@ -1,0 +1,41 @@
+"""Table of the sweep-kernel instantiations compiled into the library.
+
+Each entry is (ndim, shape, radius, bT range, storage type, mode, dtype tag).
+The build step (build.py) turns every entry into small translation units so
+that nvcc compiles them in parallel.  Degrees bT are bounded by the register
+ring each kernel keeps (bT * (2R+1) rows of 4 cells per lane): the paper's
+own tuning range is bT in [1, 16] for 2D and [1, 8] for 3D (Section 5.3),
+and its best FP32 degrees are 10/10/7/5 (star R1-4) and 10/5 (box R1-2)
+(Table 5).
+"""
+
+STAR, BOX = "SH_STAR", "SH_BOX"
+
+KERNELS_2D = [
+    # FP32 plain method
+    (STAR, 1, range(1, 11), "float", "MODE_PLAIN", "DT_F32"),
+    (STAR, 2, range(1, 9), "float", "MODE_PLAIN", "DT_F32"),
+    (STAR, 3, range(1, 6), "float", "MODE_PLAIN", "DT_F32"),
+    (STAR, 4, range(1, 5), "float", "MODE_PLAIN", "DT_F32"),
+    (BOX, 1, range(1, 11), "float", "MODE_PLAIN", "DT_F32"),
+    (BOX, 2, range(1, 7), "float", "MODE_PLAIN", "DT_F32"),
+    # FP64 plain method (FP64 fma bound on GB300: small degrees suffice)
+    (STAR, 1, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
+    (STAR, 2, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
+    (STAR, 3, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
+    (STAR, 4, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
+    (BOX, 1, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
+    (BOX, 2, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
+    # precision forms: binary16 storage, Dot2-compensated FP32
+    (STAR, 1, range(1, 11), "__half", "MODE_PLAIN", "DT_F16S"),
+    (BOX, 1, range(1, 11), "__half", "MODE_PLAIN", "DT_F16S"),
+    (STAR, 1, range(1, 9), "float", "MODE_DOT2", "DT_F32C"),
+    (BOX, 1, range(1, 9), "float", "MODE_DOT2", "DT_F32C"),
+]
+
+
+def instantiations():
+    """Yield (header, entry expression) for every kernel instantiation."""
+    for shape, r, bts, s, mode, dt in KERNELS_2D:
+        for bt in bts:
+            yield "sweep2d.cuh", f"entry2d<{shape}, {r}, {bt}, {s}, {mode}>({dt})"
