@@ -1,0 +1,449 @@
+#!/usr/bin/env python3
+"""Benchmark of the temporally blocked stencil sweep (GCell-updates/s).
+
+One step = one call of the library's run entry point advancing the workload
+grid T time steps (all passes of the N.5D-blocked sweep plus the halo copy),
+on seeded synthetic inputs of the paper's benchmark shapes (Section 5.1:
+16384^2 2D grids, 512^3 3D grids, 1000 iterations).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...    # the CPU oracle, timed on host cores
+
+Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank runs an
+independent replica of the workload on its own GPU: the sweep has no
+exchange step on one grid, so the job scales weakly with no collective on
+the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2001_01473_gb300 import inputs  # noqa: E402
+
+STAR, BOX = inputs.STAR, inputs.BOX
+
+# name -> (ndim, shape, radius, dtype, interior dims, T)
+WORKLOADS = {
+    "star2d1r-f32": (2, STAR, 1, "f32", (16384, 16384), 1000),
+    "star2d2r-f32": (2, STAR, 2, "f32", (16384, 16384), 1000),
+    "star2d3r-f32": (2, STAR, 3, "f32", (16384, 16384), 1000),
+    "star2d4r-f32": (2, STAR, 4, "f32", (16384, 16384), 1000),
+    "box2d1r-f32": (2, BOX, 1, "f32", (16384, 16384), 1000),
+    "box2d2r-f32": (2, BOX, 2, "f32", (16384, 16384), 1000),
+    "star2d1r-f64": (2, STAR, 1, "f64", (16384, 16384), 1000),
+    "star2d2r-f64": (2, STAR, 2, "f64", (16384, 16384), 1000),
+    "box2d1r-f64": (2, BOX, 1, "f64", (16384, 16384), 1000),
+    "box2d1r-f16": (2, BOX, 1, "f16", (16384, 16384), 1000),
+    "box2d1r-f32c": (2, BOX, 1, "f32c", (16384, 16384), 1000),
+    # smaller grids for profiler captures (still larger than the 129 MB L2)
+    "star2d1r-f32-8k": (2, STAR, 1, "f32", (8192, 8192), 100),
+    "box2d2r-f32-8k": (2, BOX, 2, "f32", (8192, 8192), 100),
+}
+DEFAULT_WORKLOAD = "star2d1r-f32"
+
+# The paper's V100 SXM2 "Tuned" figures (Table 5) for the same stencil,
+# precision, grid and iteration count, in GCell/s (GFLOP/s / FLOP per cell).
+PAPER_V100_GCELLS = {
+    "star2d1r-f32": 5631 / 9, "star2d2r-f32": 6319 / 17, "star2d3r-f32": 7132 / 25,
+    "star2d4r-f32": 7244 / 33, "box2d1r-f32": 6693 / 17, "box2d2r-f32": 9163 / 49,
+    "star2d1r-f64": 3306 / 9, "star2d2r-f64": 3071 / 17, "box2d1r-f64": 2984 / 17,
+}
+
+# GB300 unit counts and clock used for the ALU peak: 152 SMs x 128 FP32 lanes
+# x 2 flops x 2070 MHz.  FP64 from the FP32:FP64 ratio the device reports.
+NOMINAL_SMS = 152
+NOMINAL_FP32_LANES = 128
+NOMINAL_MAX_MHZ = 2070.0
+FALLBACK_HBM_GBS = 6800.0
+
+
+def bytes_per_cell(dtype: str) -> int:
+    return {"f32": 4, "f64": 8, "f16": 2, "f32c": 4}[dtype]
+
+
+def flops_per_cell(ndim: int, shape: int, R: int, dtype: str) -> int:
+    """Algorithmic flops of one cell-update: one multiply + (n-1) fma = 2n-1
+    (Table 4).  The compensated form counts Dot2's 10 flops per term."""
+    n = inputs.coeff_count(ndim, shape, R)
+    if dtype == "f32c":
+        return 10 * n - 8
+    return 2 * n - 1
+
+
+def load_measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            with open(p) as f:
+                d = json.load(f)
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Distributed plumbing (replicas; no collective on the data path).
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(x: float, dist, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist, device=None):
+    if dist is None:
+        return
+    import torch
+    if device is not None and str(device).startswith("cuda"):
+        dist.barrier(device_ids=[torch.cuda.current_device()])
+    else:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region.
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        mx = [num(r[2]) for r in rows]
+        pw = [num(r[3]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower() in ("active", "1", "yes")})
+        loaded = [s for s, p in zip(sm, pw) if p == p] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx),
+                "power_w_max": max(p for p in pw if p == p) if any(p == p for p in pw) else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+# Traffic from the committed ncu summary (valid only for the kernel source it
+# was taken on).
+
+def kernel_source_digest() -> str:
+    h = hashlib.sha1()
+    for f in ("sweep2d.cuh", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2001_01473_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def committed_traffic(workload: str, bt: int):
+    """dram bytes per launch of the sweep kernel recorded under profiles/ for
+    this workload and degree, if taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "sweep2d_traffic.md")
+    if not os.path.exists(p):
+        return None
+    digest = kernel_source_digest()
+    pat = re.compile(r"^\|\s*%s\s*\|\s*%d\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]+)\s*\|"
+                     % (re.escape(workload), bt))
+    with open(p) as f:
+        for line in f:
+            m = pat.match(line.strip())
+            if m and m.group(3) == digest:
+                # recorded on a smaller grid: scale by the cells of a full launch
+                return float(m.group(1)) * float(m.group(2))
+    return None
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the CPU oracle.
+
+def oracle_time(ndim, shape, R, dtype, dims, budget_s=12.0):
+    """Time the oracle on a bounded sample of the workload: the full grid for
+    a number of steps chosen so that the run takes about budget_s."""
+    import oracle
+    n = inputs.coeff_count(ndim, shape, R)
+    c = inputs.normalised_coeffs(n, 0)
+    u0 = inputs.field(dims, R, 1, dtype)
+    cells = float(np.prod(dims))
+
+    def run(T):
+        if dtype == "f64":
+            oracle.run_f64(ndim, shape, R, c, dims, u0, T)
+        elif dtype == "f16":
+            oracle.run_f16s(ndim, shape, R, c.astype(np.float32), dims, u0, T)
+        elif dtype == "f32c":
+            oracle.run_dot2(ndim, shape, R, c.astype(np.float32), dims, u0, T)
+        else:
+            oracle.run_f32(ndim, shape, R, c.astype(np.float32), dims, u0, T)
+
+    t0 = time.perf_counter()
+    run(1)
+    t1 = time.perf_counter() - t0
+    T = max(1, min(1000, int(budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    run(T)
+    dt = time.perf_counter() - t0
+    return {"value": cells * T / dt / 1e9, "unit": "GCell-updates/s", "cores": oracle.get_threads(),
+            "kind": "oracle", "seconds": round(dt, 3),
+            "sample": f"full {'x'.join(map(str, dims))} grid, T={T} of the workload's steps "
+                      f"(includes the oracle's two buffer copies)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    ndim, shape, R, dtype, dims, T = WORKLOADS[args.workload]
+    # each step is a bounded sample: the whole run stays within a few minutes
+    budget = max(2.0, min(args.ref_budget, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(max(0, args.warmup)):
+        oracle_time(ndim, shape, R, dtype, dims, budget_s=min(budget, 2.0))
+    steps = [oracle_time(ndim, shape, R, dtype, dims, budget_s=budget) for _ in range(args.steps)]
+    v = statistics.mean(s["value"] for s in steps)
+    cpu = dict(steps[0])
+    cpu["value"] = v
+    line = {
+        "impl": "reference", "metric": "GCell-updates/s", "value": v, "unit": "GCell-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(s["seconds"] for s in steps) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+        "data": "synthetic", "config": workload_config(args.workload, world),
+        "cpu_baseline": cpu,
+        "e2e": {"value": v, "unit": "GCell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(name, world):
+    ndim, shape, R, dtype, dims, T = WORKLOADS[name]
+    return {"workload": f"{name}: {'star' if shape == STAR else 'box'} radius {R}, "
+                        f"{'x'.join(map(str, dims))} interior + {R}-cell Dirichlet halo, T={T}, "
+                        f"seeded normalised coefficients, uniform [0,1) field",
+            "stencil": name, "dims": list(dims), "T": T, "radius": R,
+            "parallelism": f"replicas{world}" if world > 1 else "single",
+            "l2": "inputs larger than L2 (1 GiB+ per buffer vs 129 MB)"}
+
+
+# ---------------------------------------------------------------------------
+# Our arm.
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2001_01473_gb300 import an5d
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, "nccl")
+    ndim, shape, R, dtype, dims, T = WORKLOADS[args.workload]
+    n = inputs.coeff_count(ndim, shape, R)
+    c = inputs.normalised_coeffs(n, 0)
+    u0 = inputs.field(dims, R, 1, dtype)
+    cells = float(np.prod(dims))
+    stream = torch.cuda.current_stream()
+
+    inrun = an5d.an5d_measure_peaks(stream)        # copy / fma / smem microbenchmarks
+    plan = an5d.Plan(ndim, shape, R, c, dtype, dims)
+    plan.tune(topk=args.topk, T_probe=args.tune_T, stream=stream)
+    cfg = plan.config()
+    bt = cfg["bT"]
+    passes = T // bt + (1 if T % bt else 0)
+    launches_per_step = passes + 1 + (1 if passes > 1 else 0)   # passes + halo copies
+
+    x = torch.from_numpy(u0).to(dev)
+    y = torch.empty_like(x)
+
+    # ---- device-resident timing ----
+    for _ in range(args.warmup):
+        plan.run(x, y, T, stream)
+    torch.cuda.synchronize()
+    barrier(dist, dev)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.run(x, y, T, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    clk = clocks.stop()
+    barrier(dist, dev)
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st}: {an5d.an5d_last_error()}")
+    ms_local = ev0.elapsed_time(ev1)
+    ms = reduce_max(ms_local, dist, dev)
+    ms_step = ms / args.steps
+    value = world * cells * T * args.steps / (ms * 1e-3) / 1e9
+
+    # ---- end to end through the host-buffer entry point ----
+    hin = torch.from_numpy(u0).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    hin_np, hout_np = hin.numpy(), hout.numpy()
+    plan.run_host(hin_np, hout_np, T, stream)      # warm (allocates staging buffers)
+    barrier(dist, dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        plan.run_host(hin_np, hout_np, T, stream)
+    e2e_s = time.perf_counter() - t0
+    e2e_s = reduce_max(e2e_s, dist, dev)
+    e2e_value = world * cells * T * args.e2e_steps / e2e_s / 1e9
+    nbytes = u0.nbytes
+
+    # ---- roofline of the dominant kernel (the sweep pass) ----
+    peaks, peak_src = load_measured_peaks()
+    w = bytes_per_cell(dtype)
+    launch_s = ms_step * 1e-3 / passes            # halo copy (~us) included: conservative
+    full_passes = T // bt
+    hbm_bytes_launch = cells * 2 * w              # read once + write once per pass
+    flops_launch = cells * bt * flops_per_cell(ndim, shape, R, dtype)
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    alu_fp32 = NOMINAL_SMS * NOMINAL_FP32_LANES * 2 * NOMINAL_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
+    alu_peak = alu_fp32 if dtype != "f64" else inrun["fp64_gflops"] / 1e3
+    t_hbm = hbm_bytes_launch / (hbm_peak * 1e9)
+    t_alu = flops_launch / (alu_peak * 1e12)
+    if t_hbm >= t_alu:
+        bound, achieved, peak, unit = "hbm", hbm_bytes_launch / launch_s / 1e9, hbm_peak, "GB/s"
+    else:
+        bound, achieved, peak, unit = "alu", flops_launch / launch_s / 1e12, alu_peak, "TFLOP/s"
+    traffic = committed_traffic(args.workload, bt)
+    roof_gcells = cells * bt / max(t_hbm, t_alu) / 1e9
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": (f"{peak_src} MEASURED_PEAKS.json hbm_gbs" if bound == "hbm" else
+                                ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if dtype != "f64"
+                                 else "in-run FP64 fma microbenchmark")),
+                "kernel": f"sweep2d_kernel bT={bt}", "launches_per_step": passes,
+                "full_degree_launches": full_passes,
+                "algorithmic_bytes_per_launch": hbm_bytes_launch,
+                "algorithmic_flops_per_launch": flops_launch,
+                "temporal_roof_gcells": roof_gcells,
+                "frac_of_temporal_roof": (cells * bt / launch_s / 1e9) / roof_gcells}
+
+    base = PAPER_V100_GCELLS.get(args.workload)
+    line = {
+        "metric": "GCell-updates/s", "value": value, "unit": "GCell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": (value / world / base) if base else None,
+        "baseline_note": "paper's V100 SXM2 Tuned figure (Table 5) for this workload: context "
+                         "from other hardware" if base else None,
+        "dtype": dtype, "data": "synthetic",
+        "config": dict(workload_config(args.workload, world), bT=bt, hsn=cfg["hsn"],
+                       tile_x=cfg["tile_x"], ctas=cfg["ctas"],
+                       model_gcells=cfg["model_gcells"], tuned_gcells=cfg["measured_gcells"]),
+        "e2e": {"value": e2e_value, "unit": "GCell-updates/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roofline,
+        "inrun_peaks": inrun,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_time(ndim, shape, R, dtype, dims, budget_s=args.ref_budget)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--topk", type=int, default=6)
+    ap.add_argument("--tune-T", type=int, default=40)
+    ap.add_argument("--ref-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

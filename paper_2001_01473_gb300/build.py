@@ -11,6 +11,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -23,7 +24,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 GEN = os.path.join(BUILD, "gen")
-OBJ = os.path.join(BUILD, "obj")
+OBJ = os.path.join(BUILD, "obj-" + platform.machine())  # never reuse another host's objects
 LIB = os.path.join(BUILD, "liban5d.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -105,7 +105,8 @@ static int encode_row_map(CUtensorMap *m, const void *base, int dtype, int64_t t
     cuuint64_t dim[1] = {(cuuint64_t)total};
     cuuint32_t boxd[1] = {(cuuint32_t)box};
     cuuint32_t es[1] = {1};
-    CUresult r = fn(m, t, 1, const_cast<void *>(base), dim, nullptr, boxd, es,
+    cuuint64_t no_strides[1] = {0};  // rank 1 has no strides, but the driver wants a pointer
+    CUresult r = fn(m, t, 1, const_cast<void *>(base), dim, no_strides, boxd, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(AN5D_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
