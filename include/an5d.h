@@ -165,6 +165,32 @@ int an5d_plan_tune(an5d_plan *plan, int topk, int64_t T_probe, void *stream);
  * AN5D_ERR_TIMEOUT.  Synchronises the device.  Clears the status. */
 int an5d_plan_status(an5d_plan *plan);
 
+/* Allocation-free variant of an5d_run.  The paper has no counterpart: it is
+ * an interface for callers that cannot call cudaMalloc, such as frameworks
+ * that hand all device memory to their own pool or caching allocator (an
+ * allocation outside it can fail against its budget or fragment it), and
+ * loops that must not stall (cudaMalloc and cudaFree may synchronise the
+ * device).  It takes the stencil description of an5d_plan_create and the
+ * buffers of an5d_run, picks the blocking as an5d_plan_create would, and
+ * runs T steps with the same kernels and the same bits as an5d_run.
+ *
+ * It allocates no device memory: the ping-pong buffer and the status word
+ * live in one file-scope device array of AN5D_NOALLOC_MAX_BYTES (+256)
+ * bytes that every GPU loading this library holds until the process exits.
+ * Grids whose padded array is larger than AN5D_NOALLOC_MAX_BYTES are
+ * rejected with AN5D_ERR_INVALID_ARG.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (set-up, once per device); make that first call before any stream
+ * capture.  Every call shares the array: calls whose GPU work overlaps (from
+ * other host threads or on other streams) race and give wrong results.
+ * Synchronous: enqueues on `stream`, waits for it, and returns
+ * AN5D_ERR_TIMEOUT if a bounded device wait gave up. */
+#define AN5D_NOALLOC_MAX_BYTES (32u << 20)
+int an5d_run_noalloc(int ndim, an5d_shape shape, int radius, const double *coeffs,
+                     an5d_dtype dtype, const int64_t *dims, const void *in, void *out, int64_t T,
+                     void *stream);
+
 /* Peak rates used by the library's analytic model and by roofline reports.
  *   hbm_gbs      device copy bandwidth, read + write bytes, GB/s
  *   fp32_gflops  FP32 fma throughput, 2 flops per fma, GFLOP/s

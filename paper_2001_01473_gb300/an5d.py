@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
     L.an5d_plan_tune.restype = I
     L.an5d_plan_status.argtypes = [P]
     L.an5d_plan_status.restype = I
+    L.an5d_run_noalloc.argtypes = [I, I, I, P, I, P, P, P, I64, P]
+    L.an5d_run_noalloc.restype = I
     L.an5d_measure_peaks.argtypes = [ctypes.POINTER(an5d_peaks), P]
     L.an5d_measure_peaks.restype = I
     L.an5d_get_peaks.argtypes = [ctypes.POINTER(an5d_peaks)]
@@ -165,6 +167,17 @@ def an5d_run(plan: int, inp, out, T: int, stream=None) -> int:
 
 def an5d_run_host(plan: int, inp: np.ndarray, out: np.ndarray, T: int, stream=None) -> int:
     return _check(load().an5d_run_host(plan, _ptr(inp), _ptr(out), int(T), _stream(stream)))
+
+
+def an5d_run_noalloc(ndim: int, shape: int, radius: int, coeffs, dtype, dims, inp, out,
+                     T: int, stream=None) -> int:
+    """Allocation-free run (see an5d.h): same arguments as plan creation plus
+    the buffers of an5d_run; synchronous."""
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int64))
+    return _check(load().an5d_run_noalloc(ndim, shape, radius, c.ctypes.data, dt, d.ctypes.data,
+                                          _ptr(inp), _ptr(out), int(T), _stream(stream)))
 
 
 def an5d_plan_destroy(plan: int) -> None:

@@ -641,3 +641,120 @@ extern "C" int an5d_plan_tune(an5d_plan *p, int topk, int64_t T_probe, void *str
     }
     return ok();
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point (declared in an5d.h as an5d_run_noalloc).
+//
+// For callers that cannot call cudaMalloc: frameworks that hand all device
+// memory to their own pool or caching allocator (a stray cudaMalloc can fail
+// against that budget or fragment it) and loops that must not stall, since
+// cudaMalloc/cudaFree may synchronise the device.  The ping-pong buffer and
+// the device status word live in one file-scope device array instead of a
+// plan.  Every GPU that loads this library holds the array until the process
+// exits.  All calls share it: calls whose GPU work overlaps (other threads,
+// other streams) race on it.
+
+namespace {
+constexpr size_t NOALLOC_HEADER = 256;  // status word at offset 0; grid buffer after it
+std::mutex g_noalloc_mu;
+void *g_noalloc_base[64] = {};          // device address of the array, per device
+}  // namespace
+
+static __device__ __align__(256) unsigned char an5d_noalloc_scratch[NOALLOC_HEADER +
+                                                                    AN5D_NOALLOC_MAX_BYTES];
+
+// Once per device, with that device current: the array's device address.
+// (Host code must not pass the symbol itself to a kernel: on the host it is
+// only a stand-in, not a device address.)
+static int noalloc_base(int dev, void **out)
+{
+    if (dev < 0 || dev >= 64) return fail(AN5D_ERR_UNSUPPORTED, "device index %d >= 64", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, an5d_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(AN5D_ERR_CUDA, "cudaGetSymbolAddress(an5d_noalloc_scratch): %s",
+                        cudaGetErrorString(e));
+        g_noalloc_base[dev] = p;
+    }
+    *out = g_noalloc_base[dev];
+    return AN5D_OK;
+}
+
+extern "C" int an5d_run_noalloc(int ndim, an5d_shape shape, int radius, const double *coeffs,
+                                an5d_dtype dtype, const int64_t *dims, const void *in, void *out,
+                                int64_t T, void *stream)
+{
+    int n = an5d_coeff_count(ndim, shape, radius);
+    if (n < 0) return n;
+    if (!coeffs || !dims) return fail(AN5D_ERR_INVALID_ARG, "coeffs and dims must not be NULL");
+    if (dtype < AN5D_F32 || dtype > AN5D_F32_COMPENSATED)
+        return fail(AN5D_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    int64_t total = 1;
+    for (int i = 0; i < ndim; ++i) {
+        if (dims[i] < 1 || dims[i] > (1ll << 30))
+            return fail(AN5D_ERR_INVALID_ARG, "dims[%d] = %lld out of range", i, (long long)dims[i]);
+        total *= dims[i] + 2 * radius;
+        if (total >= (1ll << 31))
+            return fail(AN5D_ERR_UNSUPPORTED, "padded array must have fewer than 2^31 elements");
+    }
+    const size_t bytes = (size_t)total * elem_size(dtype);
+    if (bytes > (size_t)AN5D_NOALLOC_MAX_BYTES)
+        return fail(AN5D_ERR_INVALID_ARG,
+                    "an5d_run_noalloc: padded grid of %zu bytes exceeds its %zu-byte limit "
+                    "(use a plan and an5d_run)",
+                    bytes, (size_t)AN5D_NOALLOC_MAX_BYTES);
+
+    an5d_plan p;  // on the stack: owns nothing
+    p.ndim = ndim;
+    p.shape = shape;
+    p.radius = radius;
+    p.dtype = dtype;
+    p.n = n;
+    for (int i = 0; i < 3; ++i) p.dims[i] = i < ndim ? dims[i] : 0;
+    p.nz = ndim == 3 ? dims[0] : 1;
+    p.ny = dims[ndim - 2];
+    p.nx = dims[ndim - 1];
+    p.total = total;
+    p.bytes = bytes;
+    const bool dbl = dtype == AN5D_F64;
+    for (int k = 0; k < n; ++k) p.coeffs[k] = dbl ? coeffs[k] : (double)(float)coeffs[k];
+    p.bt_max = largest_bt(&p);
+    if (p.bt_max == 0)
+        return fail(AN5D_ERR_UNSUPPORTED, "stencil ndim=%d shape=%d R=%d dtype=%d is not built",
+                    ndim, (int)shape, radius, (int)dtype);
+    CUDA_TRY(cudaGetDevice(&p.device));
+    CUDA_TRY(cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, p.device));
+    void *base = nullptr;
+    if (int s = noalloc_base(p.device, &base)) return s;
+    p.d_status = static_cast<int *>(base);
+    p.scratch = static_cast<unsigned char *>(base) + NOALLOC_HEADER;
+    choose_default(&p);
+    if (int s = check_run_args(&p, in, out, T)) return s;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(p.d_status, 0, sizeof(int), st));  // the array keeps old contents
+    if (T == 0) {
+        CUDA_TRY(cudaMemcpyAsync(out, in, p.bytes, cudaMemcpyDeviceToDevice, st));
+    } else {
+        // Same pass list as an5d_run, walked without a container.
+        const int64_t full = T / p.bt;
+        const int rem = (int)(T % p.bt);
+        const int64_t np = full + (rem ? 1 : 0);
+        if (int s = launch_halo_copy(&p, in, out, st)) return s;
+        if (np > 1)
+            if (int s = launch_halo_copy(&p, in, p.scratch, st)) return s;
+        const void *src = in;
+        for (int64_t k = 0; k < np; ++k) {
+            void *dst = ((np - 1 - k) % 2 == 0) ? out : p.scratch;
+            if (int s = launch_pass(&p, k < full ? p.bt : rem, src, dst, st)) return s;
+            src = dst;
+        }
+    }
+    int h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (h & STATUS_TIMEOUT) return fail(AN5D_ERR_TIMEOUT, "a bounded device wait gave up");
+    return ok();
+}
