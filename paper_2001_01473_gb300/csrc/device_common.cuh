@@ -201,4 +201,55 @@ template <typename C> struct Acc<MODE_DOT2, C> {
     }
 };
 
+// ----------------------------------------------------------------------------
+// Packed pairs of binary32 (sm_100+ f32x2 arithmetic).  Each element of
+// fma.rn.f32x2 / mul.rn.f32x2 is one IEEE operation rounded to nearest, so a
+// packed chain gives the same bits as two scalar chains; it halves the issue
+// slots the fma chain takes.
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi)
+{
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
+{
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Store predicated by bit `bit` of `mask`, without a branch.
+template <typename S> __device__ __forceinline__ void st_pred(S *p, S v, unsigned mask, int bit);
+template <> __device__ __forceinline__ void st_pred<float>(float *p, float v, unsigned mask, int bit)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.f32 [%0], %1;\n\t}" ::"l"(p),
+                 "f"(v), "r"(mask & (1u << bit))
+                 : "memory");
+}
+template <> __device__ __forceinline__ void st_pred<double>(double *p, double v, unsigned mask, int bit)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.f64 [%0], %1;\n\t}" ::"l"(p),
+                 "d"(v), "r"(mask & (1u << bit))
+                 : "memory");
+}
+template <> __device__ __forceinline__ void st_pred<__half>(__half *p, __half v, unsigned mask, int bit)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.b16 [%0], %1;\n\t}" ::"l"(p),
+                 "h"(__half_as_ushort(v)), "r"(mask & (1u << bit))
+                 : "memory");
+}
+
 }  // namespace an5d

@@ -31,6 +31,7 @@
 #pragma once
 
 #include "an5d_internal.h"
+#include <cstring>
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -55,76 +56,58 @@ template <typename S, int N> struct Sweep2DArgs {
     int hsn;          // output rows per stream block
     int total_warps;  // tiles_x * stream blocks
     CoeffBlock<typename StorageTraits<S>::C, N> k;
+    CoeffBlock<unsigned long long, N> kp;  // FP32: (c_k, c_k) packed pairs for f32x2 arithmetic
 };
 
 template <typename S, int BT, int R> struct Sweep2DGeom {
     static constexpr int V = CELLS_PER_LANE;
+    static constexpr int P = 2 * R + 1;  // register-ring period = unroll factor
     static constexpr int A = StorageTraits<S>::ALIGN_ELEMS;
     static constexpr int TILE = 32 * V;
     static constexpr int ROWBUF = TILE + A;  // TMA box: tile + alignment slack
     static constexpr int SLOT_BYTES = ((ROWBUF * (int)sizeof(S) + 127) / 128) * 128;
-    // A row stays in the ring for bT*R iterations after it is consumed (the
-    // edge tiles re-read halo columns from it); PREFETCH_ROWS more are in flight.
-    static constexpr int D = BT * R + PREFETCH_ROWS + 1;
+    // Rows are requested PF rows ahead (a multiple of P, at least PREFETCH_ROWS).
+    static constexpr int PF = ((PREFETCH_ROWS + P - 1) / P) * P;
+    // A row stays in the ring bT*R iterations after it was consumed (edge
+    // tiles re-read their halo columns from it) while the next PF + P rows
+    // are in flight; the depth is a multiple of P so that a group of P rows
+    // occupies P consecutive slots of one mbarrier phase.
+    static constexpr int D = ((PF + P + BT * R + P - 1) / P) * P;
     // Every warp's ring starts on a 128-byte boundary (TMA destination).
     static constexpr int WARP_BYTES = ((D * SLOT_BYTES + D * 8 + 127) / 128) * 128;
     // + 128 bytes to align the dynamic shared-memory base by hand.
     static constexpr int CTA_BYTES = WARPS_PER_CTA * WARP_BYTES + 128;
     static_assert(TILE - 2 * BT * R >= 8, "tile too narrow for bT*R");
     static_assert(R <= V, "radius must not exceed cells per lane");
+    static_assert(PF <= 32, "prefetch lanes");
 };
 
-// Per-warp TMA row ring.
-template <typename S, int D, int SLOT_BYTES, int ROWBUF> struct RowRing {
-    unsigned char *base;
-    uint64_t *bars;
-    const CUtensorMap *map;
-    int pitch, x0, first_row, nrows;
-    int *status;
-
-    __device__ __forceinline__ int slot(int row) const { return pmod(row - first_row, D); }
-    __device__ __forceinline__ uint32_t parity(int row) const
-    {
-        return (uint32_t)(((row - first_row) / D) & 1);
-    }
-    // Called by one lane.
-    __device__ __forceinline__ void issue(int row) const
-    {
-        constexpr int A = StorageTraits<S>::ALIGN_ELEMS;
-        const int lin = row * pitch + x0;
-        const int s = slot(row);
-        fence_proxy_async();
-        mbar_expect_tx(&bars[s], ROWBUF * (int)sizeof(S));
-        tma_load_1d(base + s * SLOT_BYTES, map, lin - pmod(lin, A), &bars[s]);
-    }
-    __device__ __forceinline__ const S *row_ptr(int row) const
-    {
-        constexpr int A = StorageTraits<S>::ALIGN_ELEMS;
-        return reinterpret_cast<const S *>(base + slot(row) * SLOT_BYTES) + pmod(row * pitch + x0, A);
-    }
-    __device__ __forceinline__ bool wait(int row) const
-    {
-        return mbar_wait_warp(&bars[slot(row)], parity(row), status);
-    }
-    // After a failed wait: wait (bounded) for every copy still in flight so
-    // that none lands in shared memory after the warp has exited.
-    __device__ __forceinline__ void drain(int row) const
-    {
-        for (int r = row; r < row + PREFETCH_ROWS && r < nrows; ++r)
-            if (!mbar_wait_warp(&bars[slot(r)], parity(r), status)) break;
-    }
+// CTAs per SM the register budget is sized for: the level rings need
+// bT * (2R+1) * 4 values per thread, plus registers for addressing,
+// accumulators and shuffled neighbours.
+// Box stencils keep the arriving row and its shifted copies live as well.
+template <typename S, int SHAPE, int BT, int R, int MODE> struct Sweep2DOccupancy {
+    static constexpr int words =
+        (int)(sizeof(typename StorageTraits<S>::C) / 4) * (MODE == MODE_DOT2 ? 2 : 1);
+    static constexpr int regs = BT * (2 * R + 1) * CELLS_PER_LANE * words +
+                                (SHAPE == SH_STAR ? 34 + 10 * R + 20 * (words - 1)
+                                                    : 40 + 2 * (2 * R + 1) * (2 * R + 1) + 8 * R * words);
+    static constexpr int raw = 65536 / (WARPS_PER_CTA * 32 * (((regs + 7) / 8) * 8));
+    static constexpr int value = raw < 1 ? 1 : (raw > 8 ? 8 : raw);
 };
 
 template <int SHAPE, int R, int BT, typename S, int MODE>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32)
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE, BT, R, MODE>::value))
     sweep2d_kernel(const __grid_constant__ CUtensorMap tmap,
                    const Sweep2DArgs<S, NCoeff2<SHAPE, R>::value> a)
 {
     using C = typename StorageTraits<S>::C;
     using G = Sweep2DGeom<S, BT, R>;
     constexpr int V = G::V;
-    constexpr int P = 2 * R + 1;
+    constexpr int P = G::P;
     constexpr int D = G::D;
+    constexpr int A = G::A;
+    constexpr int PF = G::PF;
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int lane = threadIdx.x & 31;
@@ -136,9 +119,11 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
     const int xt = gw % a.tiles_x;
     const int sbk = gw / a.tiles_x;
     const int x0 = R - BT * R + xt * a.tile_stride;  // padded column of the tile's first cell
-    const int nrows = a.ny + 2 * R;
+    const int ny = a.ny;
+    const int pitch = a.pitch;
+    const int nrows = ny + 2 * R;
     const int y0 = R + sbk * a.hsn;                 // output rows [y0, y1)
-    const int y1 = min(y0 + a.hsn, a.ny + R);
+    const int y1 = min(y0 + a.hsn, ny + R);
     const int ys = max(0, y0 - BT * R);             // first input row needed
     const int ib0 = ys - ys % P;                    // streaming starts on a ring-period boundary
     const int iend = y1 + BT * R;                   // level bT emits row y1-1 at i = y1-1+bT*R
@@ -155,58 +140,40 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
     }
     const bool edge = __any_sync(FULL_MASK, halo_bits != 0);
 
-    RowRing<S, D, G::SLOT_BYTES, G::ROWBUF> rs;
     unsigned char *const smem_al = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
-    rs.base = smem_al + warp * G::WARP_BYTES;
-    rs.bars = reinterpret_cast<uint64_t *>(rs.base + D * G::SLOT_BYTES);
-    rs.map = &tmap;
-    rs.pitch = a.pitch;
-    rs.x0 = x0;
-    rs.first_row = ib0;
-    rs.nrows = nrows;
-    rs.status = a.status;
+    unsigned char *const ring = smem_al + warp * G::WARP_BYTES;
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(ring + D * G::SLOT_BYTES);
+    int *const status = a.status;
+
+    // TMA of padded row r into ring slot s (one lane).  The copy starts at the
+    // 16-byte boundary at or below the tile's first cell of that row.
+    auto issue = [&](int r, int s) {
+        const int lin = r * pitch + x0;
+        fence_proxy_async();
+        mbar_expect_tx(&bars[s], G::ROWBUF * (int)sizeof(S));
+        tma_load_1d(ring + s * G::SLOT_BYTES, &tmap, lin & ~(A - 1), &bars[s]);
+    };
+    auto row_in_slot = [&](int r, int s) -> const S * {
+        return reinterpret_cast<const S *>(ring + s * G::SLOT_BYTES) + ((r * pitch + x0) & (A - 1)) +
+               lane * V;
+    };
 
     if (lane == 0) {
-        for (int s = 0; s < D; ++s) mbar_init(&rs.bars[s], 1);
+        for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
-        for (int r = ib0; r < ib0 + PREFETCH_ROWS && r < nrows; ++r) rs.issue(r);
     }
     __syncwarp();
+    if (lane < PF && ib0 + lane < nrows) issue(ib0 + lane, lane);  // rows ib0 .. ib0+PF-1
+
+    // Ring position of the group that starts at row ib: slots sb .. sb+P-1,
+    // all in mbarrier phase `par`.
+    int sb = 0;
+    uint32_t par = 0;
 
     const auto &cf = a.k.c;
     S *const dst = a.dst;
-    const int pitch = a.pitch;
-    const int ny = a.ny;
 
-    // Level-0 row i -> registers; prefetch row i + PREFETCH_ROWS.
-    auto load_row = [&](int i, bool have, C (&row)[V]) -> bool {
-        if (have) {
-            if (!rs.wait(i)) {
-                rs.drain(i);
-                return false;
-            }
-            const S *src = rs.row_ptr(i) + lane * V;
-#pragma unroll
-            for (int v = 0; v < V; ++v) row[v] = load_c<S>(src[v]);
-        } else {
-#pragma unroll
-            for (int v = 0; v < V; ++v) row[v] = C(0);
-        }
-        __syncwarp();
-        if (lane == 0 && i + PREFETCH_ROWS < nrows) rs.issue(i + PREFETCH_ROWS);
-        return true;
-    };
-
-    auto store_row = [&](int j, const C (&res)[V]) {
-        S *out = dst + (j * pitch + col0);
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-            if (store_bits & (1u << v)) out[v] = to_storage<S>(res[v]);
-    };
-
-    // x-neighbours of a row held as V values per lane: L[d-1] = cell -d,
-    // Rt[d-1] = cell V-1+d (relative to the lane's first cell).
     auto exchange = [&](const C (&row)[V], C (&L)[R], C (&Rt)[R]) {
 #pragma unroll
         for (int d = 1; d <= R; ++d) {
@@ -214,24 +181,310 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
             Rt[d - 1] = __shfl_down_sync(FULL_MASK, row[d - 1], 1);
         }
     };
+    auto store_row = [&](int j, const C (&res)[V]) {
+        S *out = dst + (j * pitch + col0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) st_pred<S>(out + v, to_storage<S>(res[v]), store_bits, v);
+    };
+    // Level-0 row i (ring slot sb+k) -> registers.  Returns false on a timeout.
+    auto load_row = [&](int i, int k, bool have, C (&row)[V]) -> bool {
+        if (have) {
+            if (!mbar_wait_warp(&bars[sb + k], par, status)) return false;
+            const S *src = row_in_slot(i, sb + k);
+#pragma unroll
+            for (int v = 0; v < V; ++v) row[v] = load_c<S>(src[v]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) row[v] = C(0);
+        }
+        return true;
+    };
+    // Request the P rows of the group PF rows ahead, one lane per row.
+    auto prefetch_group = [&](int ib) {
+        __syncwarp();
+        if (lane < P) {
+            const int r = ib + PF + lane;
+            int s = sb + PF + lane;
+            if (s >= D) s -= D;
+            if (r < nrows) issue(r, s);
+        }
+    };
+    auto advance = [&]() {
+        sb += P;
+        if (sb == D) {
+            sb = 0;
+            par ^= 1u;
+        }
+    };
+    // After a timeout: wait (bounded) for every copy this warp still has in
+    // flight, so none lands in shared memory after the warp exits.
+    auto drain = [&](int ib) {
+        int s = sb;
+        uint32_t ph = par;
+        for (int r = ib; r < ib + PF + P && r < nrows; ++r) {
+            if (!mbar_wait_warp(&bars[s], ph, status)) break;
+            if (++s == D) {
+                s = 0;
+                ph ^= 1u;
+            }
+        }
+    };
 
-    if constexpr (SHAPE == SH_STAR) {
-        // ring[t][r % P] = level-t row r, t = 0..bT-1
-        C ring[BT][P][V];
+    // FP32 plain chains run on packed pairs of cells (f32x2) wherever both
+    // operands are already paired: the centre, every y-shifted row and the
+    // even x-shifts.  An odd x-shift would pair cells of two different
+    // pairs, so those terms run as scalar fmas on the two halves of the
+    // packed accumulator.  Each half still sees exactly the canonical chain.
+    constexpr bool PACKED = std::is_same<S, float>::value && MODE == MODE_PLAIN;
+    constexpr int H = V / 2;
+    const auto &cp = a.kp.c;
+
+    if constexpr (SHAPE == SH_STAR && PACKED) {
+        // rr[t][r % P][h] = cells 2h, 2h+1 of level-t row r, t = 0..bT-1
+        f2_t rr[BT][P][H];
+#pragma unroll
+        for (int t = 0; t < BT; ++t)
+#pragma unroll
+            for (int s2 = 0; s2 < P; ++s2)
+#pragma unroll
+                for (int h = 0; h < H; ++h) rr[t][s2][h] = 0ull;
+
+        auto group = [&](auto check_tag, auto edge_tag, int ib) -> bool {
+            constexpr bool CHECK = decltype(check_tag)::value;
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            prefetch_group(ib);
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int i = ib + k;
+                if (CHECK && i >= iend) return true;
+                {
+                    float row[V];
+                    if (!load_row(i, k, !CHECK || i < nrows, row)) return false;
+#pragma unroll
+                    for (int h = 0; h < H; ++h) rr[0][k][h] = f2_pack(row[2 * h], row[2 * h + 1]);
+                }
+#pragma unroll
+                for (int t = 1; t <= BT; ++t) {
+                    const int j = i - t * R;
+                    const int sj = ((k - t * R) % P + P) % P;
+                    if (CHECK && (j < R || j >= ny + R)) {
+                        if (t < BT) {
+#pragma unroll
+                            for (int h = 0; h < H; ++h) rr[t][sj][h] = rr[t - 1][sj][h];
+                        }
+                        continue;
+                    }
+                    if (CHECK && t == BT && (j < y0 || j >= y1)) continue;
+                    float x[V];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) f2_unpack(rr[t - 1][sj][h], x[2 * h], x[2 * h + 1]);
+                    float L[R], Rt[R];
+#pragma unroll
+                    for (int d = 1; d <= R; ++d) {
+                        L[d - 1] = __shfl_up_sync(FULL_MASK, x[V - d], 1);
+                        Rt[d - 1] = __shfl_down_sync(FULL_MASK, x[d - 1], 1);
+                    }
+                    f2_t acc[H];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) acc[h] = f2_mul(cp[0], rr[t - 1][sj][h]);
+                    int kk = 1;
+#pragma unroll
+                    for (int ii = -R; ii <= R; ++ii) {
+                        if (ii == 0) continue;
+                        // x-shift ii: even and inside the lane -> packed; else scalar halves
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            const int m = 2 * h + ii;
+                            if (ii % 2 == 0 && m >= 0 && m + 1 < V) {
+                                acc[h] = f2_fma(cp[kk], rr[t - 1][sj][m / 2], acc[h]);
+                            } else {
+                                float lo, hi;
+                                f2_unpack(acc[h], lo, hi);
+                                const float x0 = m < 0 ? L[-m - 1] : (m >= V ? Rt[m - V] : x[m]);
+                                const float x1 =
+                                    m + 1 < 0 ? L[-m - 2] : (m + 1 >= V ? Rt[m + 1 - V] : x[m + 1]);
+                                lo = op_fma(cf[kk], x0, lo);
+                                hi = op_fma(cf[kk], x1, hi);
+                                acc[h] = f2_pack(lo, hi);
+                            }
+                        }
+                        const int sy = ((k - t * R + ii) % P + P) % P;
+#pragma unroll
+                        for (int h = 0; h < H; ++h) acc[h] = f2_fma(cp[kk + 1], rr[t - 1][sy][h], acc[h]);
+                        kk += 2;
+                    }
+                    if (t < BT) {
+                        if (EDGE) {
+#pragma unroll
+                            for (int h = 0; h < H; ++h) {
+                                float r0, r1;
+                                f2_unpack(acc[h], r0, r1);
+                                if (halo_bits & (1u << (2 * h))) r0 = x[2 * h];
+                                if (halo_bits & (1u << (2 * h + 1))) r1 = x[2 * h + 1];
+                                acc[h] = f2_pack(r0, r1);
+                            }
+                        }
+#pragma unroll
+                        for (int h = 0; h < H; ++h) rr[t][sj][h] = acc[h];
+                    } else {
+                        float res[V];
+#pragma unroll
+                        for (int h = 0; h < H; ++h) f2_unpack(acc[h], res[2 * h], res[2 * h + 1]);
+                        store_row(j, res);
+                    }
+                }
+            }
+            return true;
+        };
+
+        for (int ib = ib0; ib < iend; ib += P) {
+            const bool fast = (ib - BT * R >= y0) && (ib + P - 1 - BT * R < y1) &&
+                              (ib - BT * R >= R) && (ib + P - 1 - R < ny + R);
+            bool ok;
+            if (fast)
+                ok = edge ? group(std::false_type{}, std::true_type{}, ib)
+                          : group(std::false_type{}, std::false_type{}, ib);
+            else
+                ok = group(std::true_type{}, std::true_type{}, ib);
+            if (!ok) {
+                drain(ib);
+                return;
+            }
+            advance();
+        }
+    } else if constexpr (SHAPE == SH_BOX && PACKED) {
+        // pa[t-1][r % P][h] = pending partial sums of cells 2h, 2h+1 of level-t row r
+        f2_t pa[BT][P][H];
+#pragma unroll
+        for (int t = 0; t < BT; ++t)
+#pragma unroll
+            for (int s2 = 0; s2 < P; ++s2)
+#pragma unroll
+                for (int h = 0; h < H; ++h) pa[t][s2][h] = 0ull;
+
+        auto group = [&](auto check_tag, auto edge_tag, int ib) -> bool {
+            constexpr bool CHECK = decltype(check_tag)::value;
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            prefetch_group(ib);
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int i = ib + k;
+                if (CHECK && i >= iend) return true;
+                float in_row[V];
+                if (!load_row(i, k, !CHECK || i < nrows, in_row)) return false;
+#pragma unroll
+                for (int t = 1; t <= BT; ++t) {
+                    const int ar = i - (t - 1) * R;
+                    // even x-shifts as pairs: XE[q + R/2] = cells 2q, 2q+1 (q may reach into
+                    // the neighbouring lanes); odd shifts use the scalar extended row e
+                    float e[V + 2 * R];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) e[R + v] = in_row[v];
+#pragma unroll
+                    for (int d = 1; d <= R; ++d) {
+                        e[R - d] = __shfl_up_sync(FULL_MASK, in_row[V - d], 1);
+                        e[R + V - 1 + d] = __shfl_down_sync(FULL_MASK, in_row[d - 1], 1);
+                    }
+                    constexpr int QL = R / 2;  // pairs needed beyond each side for even shifts
+                    f2_t XE[H + 2 * QL];
+#pragma unroll
+                    for (int q = -QL; q < H + QL; ++q)
+                        XE[q + QL] = f2_pack(e[R + 2 * q], e[R + 2 * q + 1]);
+#pragma unroll
+                    for (int dy = -R; dy <= R; ++dy) {
+                        const int b = ar - dy;
+                        const int sp = ((k - (t - 1) * R - dy) % P + P) % P;
+                        if (CHECK && (b < R || b >= ny + R)) {
+                            if (dy == 0 && t < BT) {
+#pragma unroll
+                                for (int h = 0; h < H; ++h) pa[t - 1][sp][h] = XE[h + QL];
+                            }
+                            continue;
+                        }
+#pragma unroll
+                        for (int dx = -R; dx <= R; ++dx) {
+                            const int kk = (dy + R) * P + (dx + R);
+                            const bool first = (dy == -R && dx == -R);
+#pragma unroll
+                            for (int h = 0; h < H; ++h) {
+                                if (dx % 2 == 0) {
+                                    const f2_t xv = XE[h + dx / 2 + QL];
+                                    pa[t - 1][sp][h] = first ? f2_mul(cp[kk], xv)
+                                                             : f2_fma(cp[kk], xv, pa[t - 1][sp][h]);
+                                } else {
+                                    const float x0 = e[R + 2 * h + dx], x1 = e[R + 2 * h + dx + 1];
+                                    float lo, hi;
+                                    if (first) {
+                                        lo = op_mul(cf[kk], x0);
+                                        hi = op_mul(cf[kk], x1);
+                                    } else {
+                                        f2_unpack(pa[t - 1][sp][h], lo, hi);
+                                        lo = op_fma(cf[kk], x0, lo);
+                                        hi = op_fma(cf[kk], x1, hi);
+                                    }
+                                    pa[t - 1][sp][h] = f2_pack(lo, hi);
+                                }
+                            }
+                        }
+                    }
+                    const int e_row = i - t * R;
+                    const int se = ((k - t * R) % P + P) % P;
+                    float out_row[V];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) f2_unpack(pa[t - 1][se][h], out_row[2 * h], out_row[2 * h + 1]);
+                    if (t < BT) {
+                        if (EDGE) {
+                            int s2 = sb + (k - t * R);
+                            if (s2 < 0) s2 += D;
+                            const float *orig = row_in_slot(e_row, s2);
+#pragma unroll
+                            for (int v = 0; v < V; ++v)
+                                if (halo_bits & (1u << v)) out_row[v] = orig[v];
+                        }
+#pragma unroll
+                        for (int v = 0; v < V; ++v) in_row[v] = out_row[v];
+                    } else if (!CHECK || (e_row >= y0 && e_row < y1)) {
+                        store_row(e_row, out_row);
+                    }
+                }
+            }
+            return true;
+        };
+
+        for (int ib = ib0; ib < iend; ib += P) {
+            const bool fast = (ib - BT * R >= y0) && (ib + P - 1 - BT * R < y1) &&
+                              (ib - BT * R >= R) && (ib + P - 1 + R < ny + R);
+            bool ok;
+            if (fast)
+                ok = edge ? group(std::false_type{}, std::true_type{}, ib)
+                          : group(std::false_type{}, std::false_type{}, ib);
+            else
+                ok = group(std::true_type{}, std::true_type{}, ib);
+            if (!ok) {
+                drain(ib);
+                return;
+            }
+            advance();
+        }
+    } else if constexpr (SHAPE == SH_STAR) {
+        // rr[t][r % P] = level-t row r, t = 0..bT-1
+        C rr[BT][P][V];
 #pragma unroll
         for (int t = 0; t < BT; ++t)
 #pragma unroll
             for (int s = 0; s < P; ++s)
 #pragma unroll
-                for (int v = 0; v < V; ++v) ring[t][s][v] = C(0);
+                for (int v = 0; v < V; ++v) rr[t][s][v] = C(0);
 
-        auto group = [&](auto check_tag, int ib) -> bool {
+        auto group = [&](auto check_tag, auto edge_tag, int ib) -> bool {
             constexpr bool CHECK = decltype(check_tag)::value;
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            prefetch_group(ib);
 #pragma unroll
             for (int k = 0; k < P; ++k) {
                 const int i = ib + k;
                 if (CHECK && i >= iend) return true;
-                if (!load_row(i, !CHECK || i < nrows, ring[0][k])) return false;
+                if (!load_row(i, k, !CHECK || i < nrows, rr[0][k])) return false;
 #pragma unroll
                 for (int t = 1; t <= BT; ++t) {
                     const int j = i - t * R;  // level-t row completed now
@@ -239,16 +492,16 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
                     if (CHECK && (j < R || j >= ny + R)) {  // halo row: fixed value
                         if (t < BT) {
 #pragma unroll
-                            for (int v = 0; v < V; ++v) ring[t][sj][v] = ring[t - 1][sj][v];
+                            for (int v = 0; v < V; ++v) rr[t][sj][v] = rr[t - 1][sj][v];
                         }
                         continue;
                     }
-                    if (t == BT && (j < y0 || j >= y1)) continue;
+                    if (CHECK && t == BT && (j < y0 || j >= y1)) continue;
                     C L[R], Rt[R];
-                    exchange(ring[t - 1][sj], L, Rt);
+                    exchange(rr[t - 1][sj], L, Rt);
                     Acc<MODE, C> acc[V];
 #pragma unroll
-                    for (int v = 0; v < V; ++v) acc[v].first(cf[0], ring[t - 1][sj][v]);
+                    for (int v = 0; v < V; ++v) acc[v].first(cf[0], rr[t - 1][sj][v]);
                     int kk = 1;
 #pragma unroll
                     for (int ii = -R; ii <= R; ++ii) {
@@ -256,25 +509,25 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             const int s = v + ii;
-                            const C xv = s < 0 ? L[-s - 1] : (s >= V ? Rt[s - V] : ring[t - 1][sj][s]);
+                            const C xv = s < 0 ? L[-s - 1] : (s >= V ? Rt[s - V] : rr[t - 1][sj][s]);
                             acc[v].add(cf[kk], xv);
                         }
                         const int sy = ((k - t * R + ii) % P + P) % P;
 #pragma unroll
-                        for (int v = 0; v < V; ++v) acc[v].add(cf[kk + 1], ring[t - 1][sy][v]);
+                        for (int v = 0; v < V; ++v) acc[v].add(cf[kk + 1], rr[t - 1][sy][v]);
                         kk += 2;
                     }
                     C res[V];
 #pragma unroll
                     for (int v = 0; v < V; ++v) res[v] = level_round<S>(acc[v].result());
                     if (t < BT) {
-                        if (edge) {
+                        if (EDGE) {
 #pragma unroll
                             for (int v = 0; v < V; ++v)
-                                if (halo_bits & (1u << v)) res[v] = ring[t - 1][sj][v];
+                                if (halo_bits & (1u << v)) res[v] = rr[t - 1][sj][v];
                         }
 #pragma unroll
-                        for (int v = 0; v < V; ++v) ring[t][sj][v] = res[v];
+                        for (int v = 0; v < V; ++v) rr[t][sj][v] = res[v];
                     } else {
                         store_row(j, res);
                     }
@@ -284,29 +537,42 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
         };
 
         for (int ib = ib0; ib < iend; ib += P) {
-            const bool fast = (ib - BT * R >= R) && (ib + P - 1 - R < ny + R) && (ib + P <= iend);
-            const bool ok = fast ? group(std::integral_constant<bool, false>{}, ib)
-                                 : group(std::integral_constant<bool, true>{}, ib);
-            if (!ok) return;
+            // fast: every row of the group is interior at every level and
+            // every level-bT row it completes is stored by this warp
+            const bool fast = (ib - BT * R >= y0) && (ib + P - 1 - BT * R < y1) &&
+                              (ib - BT * R >= R) && (ib + P - 1 - R < ny + R);
+            bool ok;
+            if (fast)
+                ok = edge ? group(std::false_type{}, std::true_type{}, ib)
+                          : group(std::false_type{}, std::false_type{}, ib);
+            else
+                ok = group(std::true_type{}, std::true_type{}, ib);
+            if (!ok) {
+                drain(ib);
+                return;
+            }
+            advance();
         }
     } else {
-        // acc[t-1][r % P] = pending partial sum of level-t row r, t = 1..bT
-        Acc<MODE, C> acc[BT][P][V];
+        // pa[t-1][r % P] = pending partial sum of level-t row r, t = 1..bT
+        Acc<MODE, C> pa[BT][P][V];
 #pragma unroll
         for (int t = 0; t < BT; ++t)
 #pragma unroll
             for (int s = 0; s < P; ++s)
 #pragma unroll
-                for (int v = 0; v < V; ++v) acc[t][s][v].set(C(0));
+                for (int v = 0; v < V; ++v) pa[t][s][v].set(C(0));
 
-        auto group = [&](auto check_tag, int ib) -> bool {
+        auto group = [&](auto check_tag, auto edge_tag, int ib) -> bool {
             constexpr bool CHECK = decltype(check_tag)::value;
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            prefetch_group(ib);
 #pragma unroll
             for (int k = 0; k < P; ++k) {
                 const int i = ib + k;
                 if (CHECK && i >= iend) return true;
                 C in_row[V];
-                if (!load_row(i, !CHECK || i < nrows, in_row)) return false;
+                if (!load_row(i, k, !CHECK || i < nrows, in_row)) return false;
 #pragma unroll
                 for (int t = 1; t <= BT; ++t) {
                     const int ar = i - (t - 1) * R;  // arriving level-(t-1) row
@@ -315,11 +581,11 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
 #pragma unroll
                     for (int dy = -R; dy <= R; ++dy) {
                         const int b = ar - dy;  // pending level-t row receiving its dy term
-                        const int sb = ((k - (t - 1) * R - dy) % P + P) % P;
+                        const int sp = ((k - (t - 1) * R - dy) % P + P) % P;
                         if (CHECK && (b < R || b >= ny + R)) {
                             if (dy == 0 && t < BT) {
 #pragma unroll
-                                for (int v = 0; v < V; ++v) acc[t - 1][sb][v].set(in_row[v]);
+                                for (int v = 0; v < V; ++v) pa[t - 1][sp][v].set(in_row[v]);
                             }
                             continue;
                         }
@@ -331,9 +597,9 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
                                 const int s = v + dx;
                                 const C xv = s < 0 ? L[-s - 1] : (s >= V ? Rt[s - V] : in_row[s]);
                                 if (dy == -R && dx == -R)
-                                    acc[t - 1][sb][v].first(cf[kk], xv);
+                                    pa[t - 1][sp][v].first(cf[kk], xv);
                                 else
-                                    acc[t - 1][sb][v].add(cf[kk], xv);
+                                    pa[t - 1][sp][v].add(cf[kk], xv);
                             }
                         }
                     }
@@ -341,17 +607,20 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
                     const int se = ((k - t * R) % P + P) % P;
                     C out_row[V];
 #pragma unroll
-                    for (int v = 0; v < V; ++v) out_row[v] = level_round<S>(acc[t - 1][se][v].result());
+                    for (int v = 0; v < V; ++v) out_row[v] = level_round<S>(pa[t - 1][se][v].result());
                     if (t < BT) {
-                        if (edge) {
-                            const S *orig = rs.row_ptr(e) + lane * V;
+                        if (EDGE) {
+                            // input value of row e, still in its ring slot k - t*R slots back
+                            int s = sb + (k - t * R);
+                            if (s < 0) s += D;
+                            const S *orig = row_in_slot(e, s);
 #pragma unroll
                             for (int v = 0; v < V; ++v)
                                 if (halo_bits & (1u << v)) out_row[v] = load_c<S>(orig[v]);
                         }
 #pragma unroll
                         for (int v = 0; v < V; ++v) in_row[v] = out_row[v];
-                    } else if (e >= y0 && e < y1) {
+                    } else if (!CHECK || (e >= y0 && e < y1)) {
                         store_row(e, out_row);
                     }
                 }
@@ -360,10 +629,19 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
         };
 
         for (int ib = ib0; ib < iend; ib += P) {
-            const bool fast = (ib - BT * R >= R) && (ib + P - 1 + R < ny + R) && (ib + P <= iend);
-            const bool ok = fast ? group(std::integral_constant<bool, false>{}, ib)
-                                 : group(std::integral_constant<bool, true>{}, ib);
-            if (!ok) return;
+            const bool fast = (ib - BT * R >= y0) && (ib + P - 1 - BT * R < y1) &&
+                              (ib - BT * R >= R) && (ib + P - 1 + R < ny + R);
+            bool ok;
+            if (fast)
+                ok = edge ? group(std::false_type{}, std::true_type{}, ib)
+                          : group(std::false_type{}, std::false_type{}, ib);
+            else
+                ok = group(std::true_type{}, std::true_type{}, ib);
+            if (!ok) {
+                drain(ib);
+                return;
+            }
+            advance();
         }
     }
 }
@@ -385,7 +663,13 @@ cudaError_t launch_sweep2d(const PassDesc &d, cudaStream_t st)
     a.tiles_x = d.tiles_x;
     a.hsn = d.hsn;
     a.total_warps = d.total_units;
-    for (int k = 0; k < N; ++k) a.k.c[k] = static_cast<C>(d.coeffs[k]);
+    for (int k = 0; k < N; ++k) {
+        a.k.c[k] = static_cast<C>(d.coeffs[k]);
+        const float f = static_cast<float>(d.coeffs[k]);
+        unsigned u;
+        memcpy(&u, &f, 4);
+        a.kp.c[k] = ((unsigned long long)u << 32) | u;
+    }
     auto fn = sweep2d_kernel<SHAPE, R, BT, S, MODE>;
     if (G::CTA_BYTES > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,

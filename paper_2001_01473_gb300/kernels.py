@@ -22,15 +22,15 @@ KERNELS_2D = [
     # FP64 plain method (FP64 fma bound on GB300: small degrees suffice)
     (STAR, 1, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
     (STAR, 2, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
-    (STAR, 3, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
-    (STAR, 4, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
+    (STAR, 3, range(1, 3), "double", "MODE_PLAIN", "DT_F64"),
+    (STAR, 4, range(1, 3), "double", "MODE_PLAIN", "DT_F64"),
     (BOX, 1, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
     (BOX, 2, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
     # precision forms: binary16 storage, Dot2-compensated FP32
     (STAR, 1, range(1, 11), "__half", "MODE_PLAIN", "DT_F16S"),
     (BOX, 1, range(1, 11), "__half", "MODE_PLAIN", "DT_F16S"),
     (STAR, 1, range(1, 9), "float", "MODE_DOT2", "DT_F32C"),
-    (BOX, 1, range(1, 9), "float", "MODE_DOT2", "DT_F32C"),
+    (BOX, 1, range(1, 7), "float", "MODE_DOT2", "DT_F32C"),
 ]
 
 
