@@ -162,6 +162,11 @@ __device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(
 
 enum : int { MODE_PLAIN = 0, MODE_DOT2 = 1 };
 
+// Coefficients passed by value as a kernel parameter (constant bank).
+template <typename C, int N> struct CoeffBlock {
+    C c[N];
+};
+
 // Per-point accumulator.  PLAIN: acc = c0*f0, then acc = fma(ck, fk, acc).
 // DOT2: Ogita-Rump-Oishi Dot2 -- TwoProduct by fma, TwoSum (Knuth), the
 // error terms summed separately and added at the end.

@@ -42,10 +42,6 @@ template <int SHAPE, int R> struct NCoeff2 {
     static constexpr int value = SHAPE == SH_STAR ? 4 * R + 1 : (2 * R + 1) * (2 * R + 1);
 };
 
-template <typename C, int N> struct CoeffBlock {
-    C c[N];
-};
-
 template <typename S, int N> struct Sweep2DArgs {
     S *dst;
     int *status;

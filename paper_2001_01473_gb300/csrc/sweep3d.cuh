@@ -1,0 +1,522 @@
+// sweep3d.cuh -- 2.5D-blocked, temporally blocked 3D stencil sweep (sm_103a).
+//
+// Method (AN5D, Section 3.1, Fig. 1; Section 3.2): tile the y and x axes,
+// stream along z, fuse bT time levels per pass; level t lags level t-1 by R
+// planes and its valid region shrinks by R cells per side in y and x; only
+// level bT's compute region is stored.  The z axis is cut into stream blocks
+// of hsn planes (Section 3.2, division of the streaming dimension).
+//
+// GB300 mapping (this library's design):
+//  * a CTA of NW warps owns a tile of TY = 2*NW rows (y) by 128 cells (x);
+//    each warp owns two rows, each lane 4 consecutive x cells of both rows;
+//  * input planes are staged by TMA, one 1D row copy per lane of warp 0,
+//    into a shared-memory ring of planes guarded by one mbarrier per plane;
+//  * each level keeps the 2R+1 most recent planes of the thread's 8 cells
+//    (star) or 2R+1 pending per-plane partial sums (box) in registers, in a
+//    fixed ring indexed by plane mod (2R+1) (Section 3.2 register allocation);
+//  * x neighbours travel by warp shuffles; y neighbours owned by other warps
+//    go through a double-buffered shared-memory exchange of the level's
+//    plane rows with one CTA barrier per level and plane (Section 3.2,
+//    shared-memory double buffering);
+//  * Dirichlet halo: halo planes are copied level to level; in tiles that
+//    touch the domain boundary, halo cells are reset to their input values
+//    after every level (Section 3.1).
+#pragma once
+
+#include <cstring>
+#include <type_traits>
+
+#include "an5d_internal.h"
+#include "device_common.cuh"
+
+namespace an5d {
+
+template <int SHAPE, int R> struct NCoeff3 {
+    static constexpr int value = SHAPE == SH_STAR ? 6 * R + 1 : (2 * R + 1) * (2 * R + 1) * (2 * R + 1);
+};
+
+template <typename S, int N> struct Sweep3DArgs {
+    S *dst;
+    int *status;
+    int px;           // padded row length nx + 2R
+    int py;           // padded rows per plane ny + 2R
+    int nz, ny, nx;   // interior extents
+    int tsx, tsy;     // output columns / rows per tile
+    int tiles_x, tiles_y;
+    int hsn;          // output planes per stream block
+    int total_ctas;   // tiles_x * tiles_y * stream blocks
+    CoeffBlock<typename StorageTraits<S>::C, N> k;
+};
+
+template <typename S, int SHAPE, int BT, int R, int NW> struct Sweep3DGeom {
+    static constexpr int V = CELLS_PER_LANE;
+    static constexpr int RW = 2;                 // rows per warp
+    static constexpr int TY = NW * RW;           // tile rows
+    static constexpr int TX = 32 * V;            // tile columns
+    static constexpr int P = 2 * R + 1;
+    static constexpr int A = StorageTraits<S>::ALIGN_ELEMS;
+    static constexpr int ROWBUF = TX + A;        // TMA box per row
+    static constexpr int ROW_BYTES = ((ROWBUF * (int)sizeof(S) + 127) / 128) * 128;
+    static constexpr int SLOT_BYTES = TY * ROW_BYTES;
+    static constexpr int PF = PREFETCH_ROWS;                       // planes in flight ahead
+    // box edge tiles re-read halo cells of planes up to bT*R behind
+    static constexpr int KEEP = SHAPE == SH_BOX ? BT * R : 0;
+    static constexpr int D = PF + KEEP + 1;                        // ring depth (planes)
+    using C = typename StorageTraits<S>::C;
+    static constexpr int XB_BYTES = 2 * TY * TX * (int)sizeof(C);  // y-exchange, double buffered
+    static constexpr int SMEM_BYTES = D * SLOT_BYTES + XB_BYTES + D * 8 + 128;
+    static_assert(SMEM_BYTES <= 232448, "shared memory per CTA exceeds 227 KB");
+    static_assert(TX - 2 * BT * R >= 8 && TY - 2 * BT * R >= 2, "tile too small for bT*R");
+    static_assert(R <= V, "radius must not exceed cells per lane");
+    static_assert(TY <= 32, "one TMA row per lane of warp 0");
+};
+
+template <int SHAPE, int R, int BT, typename S, int MODE, int NW>
+__global__ void __launch_bounds__(NW * 32, 1)
+    sweep3d_kernel(const __grid_constant__ CUtensorMap tmap,
+                   const Sweep3DArgs<S, NCoeff3<SHAPE, R>::value> a)
+{
+    using C = typename StorageTraits<S>::C;
+    using G = Sweep3DGeom<S, SHAPE, BT, R, NW>;
+    constexpr int V = G::V, RW = G::RW, TY = G::TY, TX = G::TX, P = G::P, D = G::D, A = G::A,
+                  PF = G::PF;
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const int cta = blockIdx.x;
+    if (cta >= a.total_ctas) return;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+
+    // ---- tile geometry ----
+    const int xt = cta % a.tiles_x;
+    const int yt = (cta / a.tiles_x) % a.tiles_y;
+    const int zb = cta / (a.tiles_x * a.tiles_y);
+    const int x0 = R - BT * R + xt * a.tsx;   // padded column of the tile's first cell
+    const int yb = R - BT * R + yt * a.tsy;   // padded row of the tile's first row
+    const int px = a.px, py = a.py, nz = a.nz, ny = a.ny, nx = a.nx;
+    const int nplanes = nz + 2 * R;
+    const int z0 = R + zb * a.hsn;
+    const int z1 = min(z0 + a.hsn, nz + R);
+    const int zs = max(0, z0 - BT * R);
+    const int ib0 = zs - zs % P;
+    const int iend = z1 + BT * R;
+
+    const int col0 = x0 + lane * V;
+    const int row0 = yb + warp * RW;          // padded row of this warp's first row
+    const int sc0 = max(R, x0 + BT * R), sc1 = min(nx + R, x0 + BT * R + a.tsx);
+    const int sr0 = max(R, yb + BT * R), sr1 = min(ny + R, yb + BT * R + a.tsy);
+    unsigned halo_bits = 0, store_bits = 0;   // bit r*V+v
+#pragma unroll
+    for (int r = 0; r < RW; ++r)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int y = row0 + r, x = col0 + v;
+            if (y < R || y >= ny + R || x < R || x >= nx + R) halo_bits |= 1u << (r * V + v);
+            if (y >= sr0 && y < sr1 && x >= sc0 && x < sc1) store_bits |= 1u << (r * V + v);
+        }
+    const bool edge = __syncthreads_or(halo_bits != 0) != 0;
+
+    unsigned char *const base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
+    unsigned char *const ring = base;
+    C *const xb = reinterpret_cast<C *>(base + D * G::SLOT_BYTES);
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(base + D * G::SLOT_BYTES + G::XB_BYTES);
+    int *const status = a.status;
+
+    // TMA of the tile rows of plane p into ring slot s: lane r of warp 0 copies row r.
+    auto issue_plane = [&](int p, int s) {
+        if (lane == 0) mbar_expect_tx(&bars[s], TY * G::ROWBUF * (int)sizeof(S));
+        __syncwarp();
+        if (lane < TY) {
+            const int lin = (p * py + yb + lane) * px + x0;
+            fence_proxy_async();
+            tma_load_1d(ring + s * G::SLOT_BYTES + lane * G::ROW_BYTES, &tmap, lin & ~(A - 1), &bars[s]);
+        }
+    };
+    // This thread's cells of tile row (warp*RW + r) of plane p in slot s.
+    auto cells_in_slot = [&](int p, int s, int r) -> const S * {
+        const int lin = (p * py + row0 + r) * px + x0;
+        return reinterpret_cast<const S *>(ring + s * G::SLOT_BYTES + (warp * RW + r) * G::ROW_BYTES) +
+               (lin & (A - 1)) + lane * V;
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0)
+        for (int q = 0; q < PF; ++q)
+            if (ib0 + q < nplanes) issue_plane(ib0 + q, q);
+
+    // Ring position of the current plane i: slot cs, mbarrier phase cpar.
+    int cs = 0;
+    uint32_t cpar = 0;
+    int xsel = 0;        // exchange buffer in use
+    // First plane whose wait gave up, with its slot and phase (-1: none).
+    int fpl = -1, fcs = 0;
+    uint32_t fpar = 0;
+
+    const auto &cf = a.k.c;
+    S *const dst = a.dst;
+
+    // Start of iteration i: request plane i+PF (its slot last held plane
+    // i+PF-D, consumed before the previous iteration's barriers), then wait
+    // for plane i and copy this thread's cells to registers.  After a wait
+    // gives up the warp stops requesting planes and keeps computing on zeros,
+    // so that every CTA barrier of the group is still reached; the pass's
+    // result is then discarded (the plan's status reports the timeout).
+    auto load_plane = [&](int i, bool have, C (&cell)[RW][V], bool &ok) {
+        if (warp == 0 && ok && i + PF < nplanes) {
+            int s = cs + PF;
+            if (s >= D) s -= D;
+            issue_plane(i + PF, s);
+        }
+        if (have && ok) {
+            ok = mbar_wait_warp(&bars[cs], cpar, status);
+            if (!ok) {
+                fpl = i;
+                fcs = cs;
+                fpar = cpar;
+            }
+        }
+        if (have && ok) {
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const S *src = cells_in_slot(i, cs, r);
+#pragma unroll
+                for (int v = 0; v < V; ++v) cell[r][v] = load_c<S>(src[v]);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < RW; ++r)
+#pragma unroll
+                for (int v = 0; v < V; ++v) cell[r][v] = C(0);
+        }
+    };
+    auto advance = [&]() {
+        if (++cs == D) {
+            cs = 0;
+            cpar ^= 1u;
+        }
+    };
+    // After a timeout: the warp that gave up waits (bounded) for the copies
+    // still in flight, planes fpl .. fpl+PF, so none lands after exit.
+    auto drain = [&](int) {
+        if (fpl < 0) return;
+        int s = fcs;
+        uint32_t ph = fpar;
+        for (int p = fpl; p <= fpl + PF && p < nplanes; ++p) {
+            if (!mbar_wait_warp(&bars[s], ph, status)) break;
+            if (++s == D) {
+                s = 0;
+                ph ^= 1u;
+            }
+        }
+    };
+    // Publish this warp's rows of a plane, then return the tile rows
+    // warp*RW - R .. warp*RW + RW - 1 + R (own rows from registers).  Rows
+    // outside the tile read a clamped row: they only feed cells outside the
+    // valid region.
+    auto exchange = [&](const C (&own)[RW][V], C (&ext)[RW + 2 * R][V]) {
+        C *buf = xb + xsel * (TY * TX);
+        xsel ^= 1;
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            C *dstp = buf + (warp * RW + r) * TX + lane * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) dstp[v] = own[r][v];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < RW + 2 * R; ++q) {
+            const int tr = warp * RW - R + q;  // tile row
+            if (q >= R && q < R + RW) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) ext[q][v] = own[q - R][v];
+            } else {
+                const int cr = tr < 0 ? 0 : (tr >= TY ? TY - 1 : tr);
+                const C *srcp = buf + cr * TX + lane * V;
+#pragma unroll
+                for (int v = 0; v < V; ++v) ext[q][v] = srcp[v];
+            }
+        }
+    };
+    auto store_cells = [&](int p, const C (&res)[RW][V]) {
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            S *out = dst + ((p * py + row0 + r) * px + col0);
+#pragma unroll
+            for (int v = 0; v < V; ++v) st_pred<S>(out + v, to_storage<S>(res[r][v]), store_bits, r * V + v);
+        }
+    };
+    // x-shifted value of tile-relative cell v+dx of a row held as V values per lane
+    auto xshift = [&](const C (&row)[V], C (&L)[R], C (&Rt)[R]) {
+#pragma unroll
+        for (int d = 1; d <= R; ++d) {
+            L[d - 1] = __shfl_up_sync(FULL_MASK, row[V - d], 1);
+            Rt[d - 1] = __shfl_down_sync(FULL_MASK, row[d - 1], 1);
+        }
+    };
+
+    if constexpr (SHAPE == SH_STAR) {
+        // ring[t][p % P][r][v] = level-t plane p at this thread's cells, t = 0..bT-1
+        C ring[BT][P][RW][V];
+#pragma unroll
+        for (int t = 0; t < BT; ++t)
+#pragma unroll
+            for (int s = 0; s < P; ++s)
+#pragma unroll
+                for (int r = 0; r < RW; ++r)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) ring[t][s][r][v] = C(0);
+
+        auto group = [&](auto check_tag, auto edge_tag, int ib) -> bool {
+            constexpr bool CHECK = decltype(check_tag)::value;
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int i = ib + k;
+                if (CHECK && i >= iend) return ok;
+                if (CHECK) __syncthreads();  // iterations of halo planes may have no exchange
+                load_plane(i, !CHECK || i < nplanes, ring[0][k], ok);
+#pragma unroll
+                for (int t = 1; t <= BT; ++t) {
+                    const int j = i - t * R;  // level-t plane completed now
+                    const int sj = ((k - t * R) % P + P) % P;
+                    if (CHECK && (j < R || j >= nz + R)) {  // halo plane: fixed value
+                        if (t < BT) {
+#pragma unroll
+                            for (int r = 0; r < RW; ++r)
+#pragma unroll
+                                for (int v = 0; v < V; ++v) ring[t][sj][r][v] = ring[t - 1][sj][r][v];
+                        }
+                        continue;
+                    }
+                    if (CHECK && t == BT && (j < z0 || j >= z1)) continue;
+                    C ext[RW + 2 * R][V];
+                    exchange(ring[t - 1][sj], ext);
+                    C res[RW][V];
+#pragma unroll
+                    for (int r = 0; r < RW; ++r) {
+                        C L[R], Rt[R];
+                        xshift(ring[t - 1][sj][r], L, Rt);
+                        Acc<MODE, C> acc[V];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v].first(cf[0], ring[t - 1][sj][r][v]);
+                        int kk = 1;
+#pragma unroll
+                        for (int ii = -R; ii <= R; ++ii) {
+                            if (ii == 0) continue;
+#pragma unroll
+                            for (int v = 0; v < V; ++v) {
+                                const int s = v + ii;
+                                const C xv = s < 0 ? L[-s - 1] : (s >= V ? Rt[s - V] : ring[t - 1][sj][r][s]);
+                                acc[v].add(cf[kk], xv);                        // dx = ii
+                            }
+#pragma unroll
+                            for (int v = 0; v < V; ++v) acc[v].add(cf[kk + 1], ext[R + r + ii][v]);  // dy = ii
+                            const int sz = ((k - t * R + ii) % P + P) % P;
+#pragma unroll
+                            for (int v = 0; v < V; ++v) acc[v].add(cf[kk + 2], ring[t - 1][sz][r][v]);  // dz = ii
+                            kk += 3;
+                        }
+#pragma unroll
+                        for (int v = 0; v < V; ++v) res[r][v] = level_round<S>(acc[v].result());
+                    }
+                    if (t < BT) {
+                        if (EDGE) {
+#pragma unroll
+                            for (int r = 0; r < RW; ++r)
+#pragma unroll
+                                for (int v = 0; v < V; ++v)
+                                    if (halo_bits & (1u << (r * V + v))) res[r][v] = ring[t - 1][sj][r][v];
+                        }
+#pragma unroll
+                        for (int r = 0; r < RW; ++r)
+#pragma unroll
+                            for (int v = 0; v < V; ++v) ring[t][sj][r][v] = res[r][v];
+                    } else {
+                        store_cells(j, res);
+                    }
+                }
+                advance();
+            }
+            return ok;
+        };
+
+        for (int ib = ib0; ib < iend; ib += P) {
+            const bool fast = (ib - BT * R >= z0) && (ib + P - 1 - BT * R < z1) &&
+                              (ib - BT * R >= R) && (ib + P - 1 - R < nz + R);
+            bool ok;
+            if (fast)
+                ok = edge ? group(std::false_type{}, std::true_type{}, ib)
+                          : group(std::false_type{}, std::false_type{}, ib);
+            else
+                ok = group(std::true_type{}, std::true_type{}, ib);
+            if (!__syncthreads_and(ok)) {
+                drain(ib);
+                return;
+            }
+        }
+    } else {
+        // pa[t-1][p % P][r][v] = pending partial sum of level-t plane p, t = 1..bT
+        Acc<MODE, C> pa[BT][P][RW][V];
+#pragma unroll
+        for (int t = 0; t < BT; ++t)
+#pragma unroll
+            for (int s = 0; s < P; ++s)
+#pragma unroll
+                for (int r = 0; r < RW; ++r)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) pa[t][s][r][v].set(C(0));
+
+        auto group = [&](auto check_tag, auto edge_tag, int ib) -> bool {
+            constexpr bool CHECK = decltype(check_tag)::value;
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int i = ib + k;
+                if (CHECK && i >= iend) return ok;
+                if (CHECK) __syncthreads();  // iterations of halo planes may have no exchange
+                C in[RW][V];
+                load_plane(i, !CHECK || i < nplanes, in, ok);
+#pragma unroll
+                for (int t = 1; t <= BT; ++t) {
+                    const int ar = i - (t - 1) * R;  // arriving level-(t-1) plane
+                    C ext[RW + 2 * R][V];
+                    exchange(in, ext);
+                    C L[RW + 2 * R][R], Rt[RW + 2 * R][R];
+#pragma unroll
+                    for (int q = 0; q < RW + 2 * R; ++q) xshift(ext[q], L[q], Rt[q]);
+#pragma unroll
+                    for (int dz = -R; dz <= R; ++dz) {
+                        const int b = ar - dz;  // pending level-t plane receiving its dz terms
+                        const int sp = ((k - (t - 1) * R - dz) % P + P) % P;
+                        if (CHECK && (b < R || b >= nz + R)) {
+                            if (dz == 0 && t < BT) {
+#pragma unroll
+                                for (int r = 0; r < RW; ++r)
+#pragma unroll
+                                    for (int v = 0; v < V; ++v) pa[t - 1][sp][r][v].set(in[r][v]);
+                            }
+                            continue;
+                        }
+#pragma unroll
+                        for (int r = 0; r < RW; ++r)
+#pragma unroll
+                            for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+                                for (int dx = -R; dx <= R; ++dx) {
+                                    const int kk = ((dz + R) * P + (dy + R)) * P + (dx + R);
+                                    const int q = R + r + dy;
+#pragma unroll
+                                    for (int v = 0; v < V; ++v) {
+                                        const int s = v + dx;
+                                        const C xv = s < 0 ? L[q][-s - 1] : (s >= V ? Rt[q][s - V] : ext[q][s]);
+                                        if (dz == -R && dy == -R && dx == -R)
+                                            pa[t - 1][sp][r][v].first(cf[kk], xv);
+                                        else
+                                            pa[t - 1][sp][r][v].add(cf[kk], xv);
+                                    }
+                                }
+                    }
+                    const int e = i - t * R;  // level-t plane completed now
+                    const int se = ((k - t * R) % P + P) % P;
+                    C out[RW][V];
+#pragma unroll
+                    for (int r = 0; r < RW; ++r)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) out[r][v] = level_round<S>(pa[t - 1][se][r][v].result());
+                    if (t < BT) {
+                        if (EDGE) {
+                            int s = cs - t * R;  // plane e = i - t*R is t*R slots back
+                            if (s < 0) s += D;
+#pragma unroll
+                            for (int r = 0; r < RW; ++r) {
+                                const S *orig = cells_in_slot(e, s, r);
+#pragma unroll
+                                for (int v = 0; v < V; ++v)
+                                    if (halo_bits & (1u << (r * V + v))) out[r][v] = load_c<S>(orig[v]);
+                            }
+                        }
+#pragma unroll
+                        for (int r = 0; r < RW; ++r)
+#pragma unroll
+                            for (int v = 0; v < V; ++v) in[r][v] = out[r][v];
+                    } else if (!CHECK || (e >= z0 && e < z1)) {
+                        store_cells(e, out);
+                    }
+                }
+                advance();
+            }
+            return ok;
+        };
+
+        for (int ib = ib0; ib < iend; ib += P) {
+            const bool fast = (ib - BT * R >= z0) && (ib + P - 1 - BT * R < z1) &&
+                              (ib - BT * R >= R) && (ib + P - 1 + R < nz + R);
+            bool ok;
+            if (fast)
+                ok = edge ? group(std::false_type{}, std::true_type{}, ib)
+                          : group(std::false_type{}, std::false_type{}, ib);
+            else
+                ok = group(std::true_type{}, std::true_type{}, ib);
+            if (!__syncthreads_and(ok)) {
+                drain(ib);
+                return;
+            }
+        }
+    }
+}
+
+template <int SHAPE, int R, int BT, typename S, int MODE, int NW>
+cudaError_t launch_sweep3d(const PassDesc &d, cudaStream_t st)
+{
+    constexpr int N = NCoeff3<SHAPE, R>::value;
+    using C = typename StorageTraits<S>::C;
+    using G = Sweep3DGeom<S, SHAPE, BT, R, NW>;
+    Sweep3DArgs<S, N> a;
+    a.dst = static_cast<S *>(d.dst);
+    a.status = d.status;
+    a.px = static_cast<int>(d.pitch);
+    a.py = static_cast<int>(d.plane / d.pitch);
+    a.nz = d.nz;
+    a.ny = d.ny;
+    a.nx = d.nx;
+    a.tsx = d.tile_stride_x;
+    a.tsy = d.tile_stride_y;
+    a.tiles_x = d.tiles_x;
+    a.tiles_y = d.tiles_y;
+    a.hsn = d.hsn;
+    a.total_ctas = d.total_units;
+    for (int k = 0; k < N; ++k) a.k.c[k] = static_cast<C>(d.coeffs[k]);
+    auto fn = sweep3d_kernel<SHAPE, R, BT, S, MODE, NW>;
+    if (G::SMEM_BYTES > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+    }
+    fn<<<d.ctas, NW * 32, G::SMEM_BYTES, st>>>(d.tmap, a);
+    return cudaGetLastError();
+}
+
+template <int SHAPE, int R, int BT, typename S, int MODE, int NW>
+KernelEntry entry3d(int dtype)
+{
+    using G = Sweep3DGeom<S, SHAPE, BT, R, NW>;
+    KernelEntry e;
+    e.key = KernelKey{3, SHAPE, R, dtype, BT};
+    e.launch = &launch_sweep3d<SHAPE, R, BT, S, MODE, NW>;
+    e.func = reinterpret_cast<const void *>(&sweep3d_kernel<SHAPE, R, BT, S, MODE, NW>);
+    e.threads = NW * 32;
+    e.smem_bytes = G::SMEM_BYTES;
+    e.tile_x = G::TX;
+    e.tile_y = G::TY;
+    e.units_per_cta = 1;
+    return e;
+}
+
+}  // namespace an5d

@@ -34,8 +34,34 @@ KERNELS_2D = [
 ]
 
 
+# 3D: (shape, radius, bT range, storage, mode, dtype, warps per CTA).  A CTA
+# tile is (2 * warps) rows by 128 cells; the register rings of the whole
+# tile (tile cells x (2R+1) planes x bT levels) must fit in one SM's
+# register file, which bounds the tile height for a given degree.
+KERNELS_3D = [
+    (STAR, 1, range(1, 4), "float", "MODE_PLAIN", "DT_F32", 16),
+    (STAR, 1, range(4, 5), "float", "MODE_PLAIN", "DT_F32", 8),
+    (STAR, 2, range(1, 2), "float", "MODE_PLAIN", "DT_F32", 16),
+    (STAR, 2, range(2, 3), "float", "MODE_PLAIN", "DT_F32", 12),
+    (STAR, 3, range(1, 2), "float", "MODE_PLAIN", "DT_F32", 16),
+    (STAR, 4, range(1, 2), "float", "MODE_PLAIN", "DT_F32", 16),
+    (BOX, 1, range(1, 3), "float", "MODE_PLAIN", "DT_F32", 16),
+    (BOX, 1, range(3, 4), "float", "MODE_PLAIN", "DT_F32", 12),
+    (STAR, 1, range(1, 2), "double", "MODE_PLAIN", "DT_F64", 16),
+    (STAR, 2, range(1, 2), "double", "MODE_PLAIN", "DT_F64", 12),
+    (STAR, 3, range(1, 2), "double", "MODE_PLAIN", "DT_F64", 8),
+    (STAR, 4, range(1, 2), "double", "MODE_PLAIN", "DT_F64", 8),
+    (BOX, 1, range(1, 2), "double", "MODE_PLAIN", "DT_F64", 12),
+    (STAR, 1, range(1, 4), "__half", "MODE_PLAIN", "DT_F16S", 16),
+    (STAR, 1, range(1, 4), "float", "MODE_DOT2", "DT_F32C", 16),
+]
+
+
 def instantiations():
     """Yield (header, entry expression) for every kernel instantiation."""
     for shape, r, bts, s, mode, dt in KERNELS_2D:
         for bt in bts:
             yield "sweep2d.cuh", f"entry2d<{shape}, {r}, {bt}, {s}, {mode}>({dt})"
+    for shape, r, bts, s, mode, dt, nw in KERNELS_3D:
+        for bt in bts:
+            yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, {mode}, {nw}>({dt})"

@@ -1,0 +1,96 @@
+"""GPU parity of the 3D (2.5D-blocked) sweeps against the CPU oracle, through
+the C ABI, bit for bit."""
+import numpy as np
+import pytest
+
+from paper_2001_01473_gb300 import an5d, inputs
+from paper_2001_01473_gb300.kernels import KERNELS_3D
+from _gpu_util import assert_bitwise, coeffs_for, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+STAR, BOX = inputs.STAR, inputs.BOX
+DT = {"DT_F32": "f32", "DT_F64": "f64", "DT_F16S": "f16", "DT_F32C": "f32c"}
+SH = {"SH_STAR": STAR, "SH_BOX": BOX}
+
+BUILT = {}
+for _sh, _r, _bts, _s, _m, _dt, _nw in KERNELS_3D:
+    BUILT.setdefault((SH[_sh], _r, DT[_dt]), []).extend(list(_bts))
+CASES = [(shape, R, dt, bt) for (shape, R, dt), bts in sorted(BUILT.items()) for bt in bts]
+
+
+@pytest.mark.parametrize("shape,R,dt,bt", CASES)
+def test_parity_3d_several_tiles_ragged(shape, R, dt, bt):
+    dims = (23, 45, 141)       # ragged tails on every axis, several tiles in x and y
+    c = coeffs_for(3, shape, R)
+    u0 = inputs.field(dims, R, 1, dt)
+    for T in sorted({1, bt, bt + 1, 2 * bt + 1}):
+        ref = oracle_run(3, shape, R, c, dt, dims, u0, T)
+        got = gpu_run(3, shape, R, c, dt, dims, u0, T, bT=bt, hsn=7)
+        assert_bitwise(got, ref, f"3d shape={shape} R={R} {dt} bT={bt} T={T}")
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (1, 5, 300), (40, 1, 1), (3, 40, 7), (9, 33, 129),
+                                  (6, 26, 122)])
+@pytest.mark.parametrize("shape,R,bt", [(STAR, 1, 3), (BOX, 1, 2), (STAR, 4, 1), (STAR, 1, 4)])
+def test_parity_3d_degenerate_extents(dims, shape, R, bt):
+    c = coeffs_for(3, shape, R, seed=5)
+    u0 = inputs.field(dims, R, 3, "f32")
+    T = 2 * bt + 1
+    ref = oracle_run(3, shape, R, c, "f32", dims, u0, T)
+    for hsn in (0, 1, 3):
+        got = gpu_run(3, shape, R, c, "f32", dims, u0, T, bT=bt, hsn=hsn)
+        assert_bitwise(got, ref, f"dims={dims} hsn={hsn}")
+
+
+def _window_reference_3d(shape, R, c, dt, u0, T, p):
+    h = T * R + R
+    lo = [max(0, q - h) for q in p]
+    hi = [min(n, q + h + 1) for q, n in zip(p, u0.shape)]
+    win = np.ascontiguousarray(u0[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]])
+    wd = tuple(s - 2 * R for s in win.shape)
+    out = oracle_run(3, shape, R, c, dt, wd, win, T)
+    return out[p[0] - lo[0], p[1] - lo[1], p[2] - lo[2]]
+
+
+@pytest.mark.parametrize("shape,R,dt", [(STAR, 1, "f32"), (BOX, 1, "f32"), (STAR, 2, "f64")])
+def test_full_size_3d_sampled(shape, R, dt):
+    import torch
+    n = 512
+    dims = (n, n, n)
+    c = coeffs_for(3, shape, R)
+    u0 = inputs.field(dims, R, 1, dt)
+    T = 10
+    with an5d.Plan(3, shape, R, c, dt, dims) as plan:
+        plan.tune(topk=3, T_probe=6)
+        x = torch.from_numpy(u0).cuda()
+        y = torch.empty_like(x)
+        plan.run(x, y, T)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        cfg = plan.config()
+        got_all = None
+    rng = np.random.default_rng(11)
+    tsx = cfg["tile_x"] - 2 * cfg["bT"] * R
+    tsy = cfg["tile_y"] - 2 * cfg["bT"] * R
+    pts = [(R, R, R), (n + R - 1, n + R - 1, n + R - 1), (R + cfg["hsn"], R + tsy, R + tsx),
+           (R + cfg["hsn"] - 1, R + tsy - 1, R + tsx - 1), (n // 2, R, n + R - 1)]
+    pts += [tuple(int(v) for v in rng.integers(R, n + R, 3)) for _ in range(16)]
+    for p in pts:
+        want = _window_reference_3d(shape, R, c, dt, u0, T, p)
+        got = y[p].item()
+        assert got == want, (p, got, want, cfg)
+    del got_all
+
+
+def test_full_size_3d_constant_field_T200():
+    import torch
+    n = 512
+    c = np.array([0.25] + [0.125] * 6)   # dyadic, sums to 1
+    with an5d.Plan(3, STAR, 1, c, "f32", (n, n, n)) as plan:
+        plan.tune(topk=3, T_probe=6)
+        x = torch.full(inputs.padded_shape((n, n, n), 1), 0.75, device="cuda")
+        y = torch.empty_like(x)
+        plan.run(x, y, 200)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        assert bool((y == 0.75).all())
