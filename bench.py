@@ -50,6 +50,13 @@ WORKLOADS = {
     "box2d1r-f64": (2, BOX, 1, "f64", (16384, 16384), 1000),
     "box2d1r-f16": (2, BOX, 1, "f16", (16384, 16384), 1000),
     "box2d1r-f32c": (2, BOX, 1, "f32c", (16384, 16384), 1000),
+    "star3d1r-f32": (3, STAR, 1, "f32", (512, 512, 512), 200),
+    "star3d2r-f32": (3, STAR, 2, "f32", (512, 512, 512), 200),
+    "star3d3r-f32": (3, STAR, 3, "f32", (512, 512, 512), 200),
+    "star3d4r-f32": (3, STAR, 4, "f32", (512, 512, 512), 200),
+    "box3d1r-f32": (3, BOX, 1, "f32", (512, 512, 512), 200),
+    "star3d1r-f64": (3, STAR, 1, "f64", (512, 512, 512), 200),
+    "box3d1r-f64": (3, BOX, 1, "f64", (512, 512, 512), 200),
     # smaller grids for profiler captures (still larger than the 129 MB L2)
     "star2d1r-f32-8k": (2, STAR, 1, "f32", (8192, 8192), 100),
     "box2d2r-f32-8k": (2, BOX, 2, "f32", (8192, 8192), 100),
@@ -62,6 +69,12 @@ PAPER_V100_GCELLS = {
     "star2d1r-f32": 5631 / 9, "star2d2r-f32": 6319 / 17, "star2d3r-f32": 7132 / 25,
     "star2d4r-f32": 7244 / 33, "box2d1r-f32": 6693 / 17, "box2d2r-f32": 9163 / 49,
     "star2d1r-f64": 3306 / 9, "star2d2r-f64": 3071 / 17, "box2d1r-f64": 2984 / 17,
+}
+# Table 5's 3D rows are for 512^3 with 1000 iterations; this benchmark runs
+# the 512^3 grids for T = 200, so they are context, not the same workload.
+PAPER_V100_3D_CONTEXT = {
+    "star3d1r-f32": 2887 / 13, "star3d2r-f32": 2910 / 25, "star3d3r-f32": 3118 / 37,
+    "star3d4r-f32": 2808 / 49, "box3d1r-f32": 6284 / 53,
 }
 
 # GB300 unit counts and clock used for the ALU peak: 152 SMs x 128 FP32 lanes
@@ -388,7 +401,7 @@ def run_ours(args, rank, world, local):
                 "peak_source": (f"{peak_src} MEASURED_PEAKS.json hbm_gbs" if bound == "hbm" else
                                 ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if dtype != "f64"
                                  else "in-run FP64 fma microbenchmark")),
-                "kernel": f"sweep2d_kernel bT={bt}", "launches_per_step": passes,
+                "kernel": f"sweep{ndim}d_kernel bT={bt}", "launches_per_step": passes,
                 "full_degree_launches": full_passes,
                 "algorithmic_bytes_per_launch": hbm_bytes_launch,
                 "algorithmic_flops_per_launch": flops_launch,
@@ -424,6 +437,80 @@ def run_ours(args, rank, world, local):
     return 0
 
 
+PRECISION_WORKLOADS = {
+    # name -> (ndim, shape, radius, coefficient recipe, dims, T)
+    "heat3d": (3, STAR, 1, "heat", (512, 512, 512), 1000),
+    "box2d1r": (2, BOX, 1, "normalised", (16384, 16384), 1000),
+}
+
+
+def run_precision(args, rank, world, local):
+    """Precision forms: throughput of the FP32 plain, Dot2-compensated FP32 and
+    binary16-storage forms next to their max / relative-L2 error against an
+    FP64 evaluation of the same sweep from the same input.  The FP64
+    evaluation is the library's FP64 plain method, which the parity tests
+    show to be bit-identical to the FP64 CPU oracle."""
+    import torch
+    from paper_2001_01473_gb300 import an5d
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    names = [args.precision_workload] if args.precision_workload else list(PRECISION_WORKLOADS)
+    for name in names:
+        ndim, shape, R, recipe, dims, T = PRECISION_WORKLOADS[name]
+        n = inputs.coeff_count(ndim, shape, R)
+        c = inputs.heat_coeffs(ndim) if recipe == "heat" else inputs.normalised_coeffs(n, 0)
+        c32 = c.astype(np.float32).astype(np.float64)
+        cells = float(np.prod(dims))
+        base32 = inputs.gaussian_bump(dims, R, 1, "f32")
+        refs = {}
+        for form in ("f32", "f32c", "f16"):
+            u0 = base32 if form != "f16" else base32.astype(np.float16)
+            key = "f16" if form == "f16" else "f32"
+            if key not in refs:                 # FP64 reference from this form's input
+                r_in = torch.from_numpy(u0.astype(np.float64)).to(dev)
+                r_out = torch.empty_like(r_in)
+                with an5d.Plan(ndim, shape, R, c32, "f64", dims) as rp:
+                    rp.run(r_in, r_out, T, stream)
+                    torch.cuda.synchronize()
+                    assert rp.status() == 0
+                del r_in
+                refs[key] = r_out
+            x = torch.from_numpy(u0).to(dev)
+            y = torch.empty_like(x)
+            with an5d.Plan(ndim, shape, R, c, form, dims) as plan:
+                plan.tune(topk=args.topk, T_probe=args.tune_T, stream=stream)
+                cfg = plan.config()
+                for _ in range(args.warmup):
+                    plan.run(x, y, T, stream)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    plan.run(x, y, T, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                assert plan.status() == 0
+                ms = e0.elapsed_time(e1) / args.steps
+            err = an5d.an5d_error_norms(ndim, R, dims, form, y, refs[key], stream)
+            umax = float(np.max(np.abs(u0.astype(np.float64))))
+            line = {"mode": "precision", "workload": name, "form": form,
+                    "metric": "GCell-updates/s", "value": cells * T / (ms * 1e-3) / 1e9,
+                    "unit": "GCell-updates/s", "ms_per_step": ms, "steps": args.steps,
+                    "config": {"dims": list(dims), "T": T, "bT": cfg["bT"], "hsn": cfg["hsn"],
+                               "init": "Gaussian bump (sigma n/8) + 0.01 U[0,1)",
+                               "coefficients": recipe},
+                    "error_vs_fp64": {"max_abs": err["max_abs"], "rel_l2": err["rel_l2"],
+                                      "max_abs_over_max_u0": err["max_abs"] / umax}}
+            if rank == 0:
+                print(json.dumps(line), flush=True)
+            del x, y
+        refs.clear()
+        torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,12 +523,17 @@ def main():
     ap.add_argument("--tune-T", type=int, default=40)
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", action="store_true",
+                    help="report the precision forms (throughput and error vs FP64)")
+    ap.add_argument("--precision-workload", default=None, choices=sorted(PRECISION_WORKLOADS))
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.precision:
+        return run_precision(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 

@@ -191,6 +191,19 @@ int an5d_run_noalloc(int ndim, an5d_shape shape, int radius, const double *coeff
                      an5d_dtype dtype, const int64_t *dims, const void *in, void *out, int64_t T,
                      void *stream);
 
+/* Error norms of a run against an FP64 reference, over the interior of a
+ * padded grid.  The precision forms are judged against an FP64 evaluation
+ * of the same sweep; FP64 arithmetic on the GPU is otherwise used only by
+ * the FP64 plain method.  (No counterpart in the paper, which reports no
+ * accuracy figures.)
+ *   u     device array of the storage type of `dtype`, padded layout
+ *   ref   device FP64 array of the same padded shape
+ *   out   host array of 3 doubles: max |u - ref|, sum (u - ref)^2, sum ref^2
+ * FP64 accumulation over a fixed partition: deterministic for a given grid.
+ * Allocates and frees a small device buffer; synchronous on `stream`. */
+int an5d_error_norms(int ndim, int radius, const int64_t *dims, an5d_dtype dtype, const void *u,
+                     const double *ref, double *out, void *stream);
+
 /* Peak rates used by the library's analytic model and by roofline reports.
  *   hbm_gbs      device copy bandwidth, read + write bytes, GB/s
  *   fp32_gflops  FP32 fma throughput, 2 flops per fma, GFLOP/s

@@ -88,6 +88,8 @@ def load(path: str = LIB_PATH):
     L.an5d_plan_status.restype = I
     L.an5d_run_noalloc.argtypes = [I, I, I, P, I, P, P, P, I64, P]
     L.an5d_run_noalloc.restype = I
+    L.an5d_error_norms.argtypes = [I, I, P, I, P, P, P, P]
+    L.an5d_error_norms.restype = I
     L.an5d_measure_peaks.argtypes = [ctypes.POINTER(an5d_peaks), P]
     L.an5d_measure_peaks.restype = I
     L.an5d_get_peaks.argtypes = [ctypes.POINTER(an5d_peaks)]
@@ -178,6 +180,18 @@ def an5d_run_noalloc(ndim: int, shape: int, radius: int, coeffs, dtype, dims, in
     d = np.ascontiguousarray(np.asarray(dims, dtype=np.int64))
     return _check(load().an5d_run_noalloc(ndim, shape, radius, c.ctypes.data, dt, d.ctypes.data,
                                           _ptr(inp), _ptr(out), int(T), _stream(stream)))
+
+
+def an5d_error_norms(ndim: int, radius: int, dims, dtype, u, ref, stream=None) -> dict:
+    """FP64 error norms of device array u against device FP64 array ref."""
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int64))
+    out = np.zeros(3, dtype=np.float64)
+    _check(load().an5d_error_norms(ndim, radius, d.ctypes.data, dt, _ptr(u), _ptr(ref),
+                                   out.ctypes.data, _stream(stream)))
+    return {"max_abs": float(out[0]), "l2_diff": float(np.sqrt(out[1])),
+            "l2_ref": float(np.sqrt(out[2])),
+            "rel_l2": float(np.sqrt(out[1] / out[2])) if out[2] > 0 else float("nan")}
 
 
 def an5d_plan_destroy(plan: int) -> None:

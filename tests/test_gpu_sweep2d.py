@@ -174,3 +174,30 @@ def test_full_size_constant_field_T1000():
         torch.cuda.synchronize()
         assert plan.status() == 0
         assert bool((y == 0.75).all())
+
+
+@pytest.mark.parametrize("shape,R,dt", [(BOX, 1, "f32c"), (BOX, 1, "f16")])
+def test_full_size_precision_forms_sampled(shape, R, dt):
+    """The precision-form kernels at 16384^2 in their tuned configuration,
+    checked cell by cell against the oracle's Dot2 / binary16 forms."""
+    import torch
+    n = 16384
+    dims = (n, n)
+    c = coeffs_for(2, shape, R)
+    u0 = inputs.field(dims, R, 1, dt)
+    T = 30
+    with an5d.Plan(2, shape, R, c, dt, dims) as plan:
+        plan.tune(topk=3, T_probe=10)
+        x = torch.from_numpy(u0).cuda()
+        y = torch.empty_like(x)
+        plan.run(x, y, T)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        cfg = plan.config()
+    rng = np.random.default_rng(3)
+    pts = [(R, R), (n + R - 1, n // 2), (R + cfg["hsn"], R + 100)]
+    pts += [tuple(int(v) for v in rng.integers(R, n + R, 2)) for _ in range(12)]
+    for (yy, xx) in pts:
+        want = _window_reference(shape, R, c, dt, u0, T, yy, xx)
+        got = y[yy, xx].item()
+        assert got == float(want), (yy, xx, got, want, cfg)

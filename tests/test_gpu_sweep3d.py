@@ -94,3 +94,27 @@ def test_full_size_3d_constant_field_T200():
         torch.cuda.synchronize()
         assert plan.status() == 0
         assert bool((y == 0.75).all())
+
+
+@pytest.mark.parametrize("dt", ["f32c", "f16"])
+def test_full_size_3d_heat_precision_forms_sampled(dt):
+    import torch
+    n = 512
+    dims = (n, n, n)
+    c = inputs.heat_coeffs(3)
+    u0 = inputs.gaussian_bump(dims, 1, 1, dt if dt != "f32c" else "f32")
+    T = 8
+    with an5d.Plan(3, STAR, 1, c, dt, dims) as plan:
+        plan.tune(topk=3, T_probe=4)
+        x = torch.from_numpy(u0).cuda()
+        y = torch.empty_like(x)
+        plan.run(x, y, T)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+    rng = np.random.default_rng(5)
+    pts = [(1, 1, 1), (n // 2, n // 2, n // 2)] + \
+          [tuple(int(v) for v in rng.integers(1, n + 1, 3)) for _ in range(8)]
+    for p in pts:
+        want = _window_reference_3d(STAR, 1, c, dt, u0, T, p)
+        got = y[p].item()
+        assert got == float(want), (p, got, want)
