@@ -511,6 +511,64 @@ def run_precision(args, rank, world, local):
     return 0
 
 
+def run_batch(args, rank, world, local):
+    """Batched form: 512 independent 2D FP32 grids (sides log-uniform in
+    [128, 4096], star/box radius 1-2, T uniform in [10, 500]) advanced by one
+    CUDA-graph launch of the persistent kernel per step."""
+    import torch
+    from paper_2001_01473_gb300 import an5d
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    descs = inputs.batch_descs()
+    grids = []
+    for i, d in enumerate(descs):
+        n = inputs.coeff_count(2, d.shape, d.radius)
+        grids.append((d.shape, d.radius, inputs.normalised_coeffs(n, 100 + i), d.ny, d.nx, d.T))
+    xs = [torch.from_numpy(inputs.field((g[3], g[4]), g[1], 500 + i, "f32")).to(dev)
+          for i, g in enumerate(grids)]
+    ys = [torch.empty_like(x) for x in xs]
+    with an5d.Batch(grids) as b:
+        info = b.tune(stream)
+        for _ in range(args.warmup):
+            b.run(xs, ys, stream)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            b.run(xs, ys, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        assert b.status() == 0, an5d.an5d_batch_last_error()
+        ms = e0.elapsed_time(e1) / args.steps
+    cells = info["cell_updates"]
+    # HBM bound: every pass reads and writes each grid once (4 + 4 bytes per cell)
+    peaks, src = load_measured_peaks()
+    passes_bytes = 0.0
+    bt_of = {(STAR, 1): info["class_bt"][0], (STAR, 2): info["class_bt"][1],
+             (BOX, 1): info["class_bt"][2], (BOX, 2): info["class_bt"][3]}
+    for g in grids:
+        bt = bt_of[(g[0], g[1])]
+        passes = g[5] // bt + g[5] % bt
+        passes_bytes += passes * g[3] * g[4] * 8.0
+    t_hbm = passes_bytes / (float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) * 1e9)
+    line = {"mode": "batch", "metric": "GCell-updates/s", "value": cells / (ms * 1e-3) / 1e9,
+            "unit": "GCell-updates/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+            "config": {"grids": len(grids), "cell_updates_per_step": cells, "items": info["items"],
+                       "persistent_ctas": info["ctas"], "class_bt": info["class_bt"],
+                       "recipe": "sides log-uniform [128,4096], star/box R1-2, T U[10,500], seed 3"},
+            "roofline": {"bound": "hbm", "hbm_time_ms": t_hbm * 1e3, "frac": t_hbm / (ms * 1e-3),
+                         "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs"},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -526,6 +584,7 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="report the precision forms (throughput and error vs FP64)")
     ap.add_argument("--precision-workload", default=None, choices=sorted(PRECISION_WORKLOADS))
+    ap.add_argument("--batch", action="store_true", help="report the batched form (512 grids)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -534,6 +593,8 @@ def main():
         return run_reference(args, rank, world)
     if args.precision:
         return run_precision(args, rank, world, local)
+    if args.batch:
+        return run_batch(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 

@@ -204,6 +204,59 @@ int an5d_run_noalloc(int ndim, an5d_shape shape, int radius, const double *coeff
 int an5d_error_norms(int ndim, int radius, const int64_t *dims, an5d_dtype dtype, const void *u,
                      const double *ref, double *out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many independent 2D FP32 grids of uneven size, stencil and
+ * length in one persistent launch replayed as a CUDA graph.  (No counterpart
+ * in the paper; each grid gets exactly the bits of an5d_run on that grid.)
+ * ------------------------------------------------------------------------ */
+
+/* One grid of a batch. */
+typedef struct {
+    an5d_shape shape;
+    int radius;            /* 1 or 2 */
+    const double *coeffs;  /* host, an5d_coeff_count(2, shape, radius) values, canonical order */
+    int64_t ny, nx;        /* interior extents (padded: +2R each) */
+    int64_t T;             /* time steps of this grid, >= 0 */
+} an5d_grid_desc;
+
+typedef struct an5d_batch_plan an5d_batch_plan;
+
+typedef struct {
+    int grids;
+    int ctas;              /* persistent CTAs (resident capacity of the device) */
+    int64_t items;         /* (grid, x tile, stream block, pass) work items */
+    double cell_updates;   /* sum over grids of ny * nx * T */
+    int class_bt[4];       /* degree per class: star R1, star R2, box R1, box R2 */
+} an5d_batch_info_t;
+
+/* Create a batch plan: copies descs and coefficients, allocates one scratch
+ * grid per grid, the work-item list and the tile pass counters on the
+ * current device.  Degrees start at 8/4/4/2 (star R1/R2, box R1/R2).
+ * Returns NULL on failure (message: an5d_batch_last_error). */
+an5d_batch_plan *an5d_batch_plan_create(int n, const an5d_grid_desc *descs);
+
+/* Pick each class's degree among the built ones {1,4,8} (radius 1) and
+ * {1,2,4} (radius 2) by timing a 1024^2 grid of the class (Section 5.3's
+ * tuning, per stencil class).  Synchronous. */
+int an5d_batch_tune(an5d_batch_plan *bp, void *stream);
+
+/* Force the degree of each class (class_bt[4], values from the built menu). */
+int an5d_batch_set_degrees(an5d_batch_plan *bp, const int *class_bt);
+
+/* Advance every grid i by its T: outs[i] = S_i^{T_i}(ins[i]).  ins/outs are
+ * host arrays of n device pointers to padded FP32 grids (16-byte aligned,
+ * out must not overlap in).  Asynchronous on `stream`: one CUDA-graph launch
+ * (counter reset, halo copies, the persistent kernel).  Not thread-safe per
+ * plan.  Device-side failures: an5d_batch_status. */
+int an5d_batch_run(an5d_batch_plan *bp, const void *const *ins, void *const *outs, void *stream);
+
+/* AN5D_OK or AN5D_ERR_TIMEOUT for the finished batch runs.  Synchronises. */
+int an5d_batch_status(an5d_batch_plan *bp);
+
+int an5d_batch_info(const an5d_batch_plan *bp, an5d_batch_info_t *info);
+const char *an5d_batch_last_error(void);
+void an5d_batch_plan_destroy(an5d_batch_plan *bp);
+
 /* Peak rates used by the library's analytic model and by roofline reports.
  *   hbm_gbs      device copy bandwidth, read + write bytes, GB/s
  *   fp32_gflops  FP32 fma throughput, 2 flops per fma, GFLOP/s

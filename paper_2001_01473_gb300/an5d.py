@@ -48,6 +48,21 @@ class an5d_config(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class an5d_grid_desc(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int), ("radius", ctypes.c_int),
+                ("coeffs", ctypes.c_void_p), ("ny", ctypes.c_int64), ("nx", ctypes.c_int64),
+                ("T", ctypes.c_int64)]
+
+
+class an5d_batch_info_t(ctypes.Structure):
+    _fields_ = [("grids", ctypes.c_int), ("ctas", ctypes.c_int), ("items", ctypes.c_int64),
+                ("cell_updates", ctypes.c_double), ("class_bt", ctypes.c_int * 4)]
+
+    def as_dict(self) -> dict:
+        return {"grids": self.grids, "ctas": self.ctas, "items": self.items,
+                "cell_updates": self.cell_updates, "class_bt": list(self.class_bt)}
+
+
 class an5d_peaks(ctypes.Structure):
     _fields_ = [("hbm_gbs", ctypes.c_double), ("fp32_gflops", ctypes.c_double),
                 ("fp64_gflops", ctypes.c_double), ("smem_gbs", ctypes.c_double),
@@ -90,6 +105,22 @@ def load(path: str = LIB_PATH):
     L.an5d_run_noalloc.restype = I
     L.an5d_error_norms.argtypes = [I, I, P, I, P, P, P, P]
     L.an5d_error_norms.restype = I
+    L.an5d_batch_plan_create.argtypes = [I, P]
+    L.an5d_batch_plan_create.restype = P
+    L.an5d_batch_tune.argtypes = [P, P]
+    L.an5d_batch_tune.restype = I
+    L.an5d_batch_set_degrees.argtypes = [P, P]
+    L.an5d_batch_set_degrees.restype = I
+    L.an5d_batch_run.argtypes = [P, P, P, P]
+    L.an5d_batch_run.restype = I
+    L.an5d_batch_status.argtypes = [P]
+    L.an5d_batch_status.restype = I
+    L.an5d_batch_info.argtypes = [P, ctypes.POINTER(an5d_batch_info_t)]
+    L.an5d_batch_info.restype = I
+    L.an5d_batch_last_error.argtypes = []
+    L.an5d_batch_last_error.restype = ctypes.c_char_p
+    L.an5d_batch_plan_destroy.argtypes = [P]
+    L.an5d_batch_plan_destroy.restype = None
     L.an5d_measure_peaks.argtypes = [ctypes.POINTER(an5d_peaks), P]
     L.an5d_measure_peaks.restype = I
     L.an5d_get_peaks.argtypes = [ctypes.POINTER(an5d_peaks)]
@@ -262,6 +293,104 @@ class Plan:
     def close(self) -> None:
         if self.handle:
             an5d_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Batched form.
+
+def an5d_batch_last_error() -> str:
+    return load().an5d_batch_last_error().decode()
+
+
+def _bcheck(rc: int) -> int:
+    if rc != AN5D_OK:
+        raise An5dError(rc, an5d_batch_last_error())
+    return rc
+
+
+def an5d_batch_plan_create(grids) -> tuple:
+    """grids: list of (shape, radius, coeffs, ny, nx, T).  Returns (handle, keepalive)."""
+    keep = [np.ascontiguousarray(np.asarray(g[2], dtype=np.float64)) for g in grids]
+    arr = (an5d_grid_desc * len(grids))()
+    for i, g in enumerate(grids):
+        arr[i] = an5d_grid_desc(int(g[0]), int(g[1]), keep[i].ctypes.data, int(g[3]), int(g[4]),
+                                int(g[5]))
+    h = load().an5d_batch_plan_create(len(grids), ctypes.cast(arr, ctypes.c_void_p))
+    if not h:
+        raise An5dError(AN5D_ERR_INVALID_ARG, an5d_batch_last_error())
+    return h, (keep, arr)
+
+
+def an5d_batch_tune(bp: int, stream=None) -> int:
+    return _bcheck(load().an5d_batch_tune(bp, _stream(stream)))
+
+
+def an5d_batch_set_degrees(bp: int, class_bt) -> int:
+    a = (ctypes.c_int * 4)(*[int(x) for x in class_bt])
+    return _bcheck(load().an5d_batch_set_degrees(bp, ctypes.cast(a, ctypes.c_void_p)))
+
+
+def an5d_batch_run(bp: int, ins, outs, stream=None) -> int:
+    n = len(ins)
+    pi = (ctypes.c_void_p * n)(*[_ptr(x) for x in ins])
+    po = (ctypes.c_void_p * n)(*[_ptr(x) for x in outs])
+    return _bcheck(load().an5d_batch_run(bp, ctypes.cast(pi, ctypes.c_void_p),
+                                         ctypes.cast(po, ctypes.c_void_p), _stream(stream)))
+
+
+def an5d_batch_status(bp: int) -> int:
+    return load().an5d_batch_status(bp)
+
+
+def an5d_batch_info(bp: int) -> dict:
+    info = an5d_batch_info_t()
+    _bcheck(load().an5d_batch_info(bp, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def an5d_batch_plan_destroy(bp: int) -> None:
+    load().an5d_batch_plan_destroy(bp)
+
+
+class Batch:
+    """RAII wrapper of a batch plan; grids = [(shape, radius, coeffs, ny, nx, T), ...]."""
+
+    def __init__(self, grids):
+        self.grids = list(grids)
+        self.handle, self._keep = an5d_batch_plan_create(self.grids)
+
+    def tune(self, stream=None) -> dict:
+        an5d_batch_tune(self.handle, stream)
+        return self.info()
+
+    def set_degrees(self, class_bt) -> None:
+        an5d_batch_set_degrees(self.handle, class_bt)
+
+    def run(self, ins, outs, stream=None) -> None:
+        an5d_batch_run(self.handle, ins, outs, stream)
+
+    def status(self) -> int:
+        return an5d_batch_status(self.handle)
+
+    def info(self) -> dict:
+        return an5d_batch_info(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            an5d_batch_plan_destroy(self.handle)
             self.handle = 0
 
     def __enter__(self):

@@ -92,10 +92,25 @@ template <typename S, int SHAPE, int BT, int R, int MODE> struct Sweep2DOccupanc
     static constexpr int value = raw < 1 ? 1 : (raw > 8 ? 8 : raw);
 };
 
-template <int SHAPE, int R, int BT, typename S, int MODE>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE, BT, R, MODE>::value))
-    sweep2d_kernel(const __grid_constant__ CUtensorMap tmap,
-                   const Sweep2DArgs<S, NCoeff2<SHAPE, R>::value> a)
+// Geometry of one warp tile of one pass.
+struct Tile2D {
+    int pitch;     // padded row length nx + 2R (elements)
+    int ny, nx;    // interior extents
+    int x0;        // padded column of the tile's first cell
+    int sc0, sc1;  // columns stored by this tile: [sc0, sc1)
+    int y0, y1;    // rows stored by this tile (its stream block): [y0, y1)
+};
+
+// One warp advances one tile of one stream block by BT time levels: it
+// streams the source rows through its TMA ring and level registers and
+// stores the level-BT rows [y0, y1) x [sc0, sc1).  The caller owns the
+// warp's shared-memory ring (Sweep2DGeom::WARP_BYTES, 128-byte aligned).
+// cf[k] are the coefficients, cp[k] the same as packed (c_k, c_k) pairs
+// (used when PACK).  Returns false if a bounded wait gave up.
+template <int SHAPE, int R, int BT, typename S, int MODE, bool PACK, typename CF, typename CP>
+__device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap *tmap, S *const dst,
+                                             int *const status, unsigned char *const ring,
+                                             const CF &cf, const CP &cp)
 {
     using C = typename StorageTraits<S>::C;
     using G = Sweep2DGeom<S, BT, R>;
@@ -104,43 +119,28 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
     constexpr int D = G::D;
     constexpr int A = G::A;
     constexpr int PF = G::PF;
-    extern __shared__ __align__(128) unsigned char smem[];
 
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int gw = blockIdx.x * WARPS_PER_CTA + warp;
-    if (gw >= a.total_warps) return;
-
-    // ---- tile geometry (Section 3.1) ----
-    const int xt = gw % a.tiles_x;
-    const int sbk = gw / a.tiles_x;
-    const int x0 = R - BT * R + xt * a.tile_stride;  // padded column of the tile's first cell
-    const int ny = a.ny;
-    const int pitch = a.pitch;
+    const int x0 = tg.x0;
+    const int ny = tg.ny;
+    const int pitch = tg.pitch;
     const int nrows = ny + 2 * R;
-    const int y0 = R + sbk * a.hsn;                 // output rows [y0, y1)
-    const int y1 = min(y0 + a.hsn, ny + R);
+    const int y0 = tg.y0, y1 = tg.y1;
     const int ys = max(0, y0 - BT * R);             // first input row needed
     const int ib0 = ys - ys % P;                    // streaming starts on a ring-period boundary
     const int iend = y1 + BT * R;                   // level bT emits row y1-1 at i = y1-1+bT*R
+    const int rend = min(nrows, iend);              // rows requested: exactly the rows consumed
 
     const int col0 = x0 + lane * V;
-    const int sc0 = max(R, x0 + BT * R);
-    const int sc1 = min(a.nx + R, x0 + BT * R + a.tile_stride);
     unsigned halo_bits = 0, store_bits = 0;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const int col = col0 + v;
-        if (col < R || col >= a.nx + R) halo_bits |= 1u << v;
-        if (col >= sc0 && col < sc1) store_bits |= 1u << v;
+        if (col < R || col >= tg.nx + R) halo_bits |= 1u << v;
+        if (col >= tg.sc0 && col < tg.sc1) store_bits |= 1u << v;
     }
     const bool edge = __any_sync(FULL_MASK, halo_bits != 0);
-
-    unsigned char *const smem_al = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
-    unsigned char *const ring = smem_al + warp * G::WARP_BYTES;
     uint64_t *const bars = reinterpret_cast<uint64_t *>(ring + D * G::SLOT_BYTES);
-    int *const status = a.status;
 
     // TMA of padded row r into ring slot s (one lane).  The copy starts at the
     // 16-byte boundary at or below the tile's first cell of that row.
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
         const int lin = r * pitch + x0;
         fence_proxy_async();
         mbar_expect_tx(&bars[s], G::ROWBUF * (int)sizeof(S));
-        tma_load_1d(ring + s * G::SLOT_BYTES, &tmap, lin & ~(A - 1), &bars[s]);
+        tma_load_1d(ring + s * G::SLOT_BYTES, tmap, lin & ~(A - 1), &bars[s]);
     };
     auto row_in_slot = [&](int r, int s) -> const S * {
         return reinterpret_cast<const S *>(ring + s * G::SLOT_BYTES) + ((r * pitch + x0) & (A - 1)) +
@@ -160,15 +160,12 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
         fence_mbar_init();
     }
     __syncwarp();
-    if (lane < PF && ib0 + lane < nrows) issue(ib0 + lane, lane);  // rows ib0 .. ib0+PF-1
+    if (lane < PF && ib0 + lane < rend) issue(ib0 + lane, lane);  // rows ib0 .. ib0+PF-1
 
     // Ring position of the group that starts at row ib: slots sb .. sb+P-1,
     // all in mbarrier phase `par`.
     int sb = 0;
     uint32_t par = 0;
-
-    const auto &cf = a.k.c;
-    S *const dst = a.dst;
 
     auto exchange = [&](const C (&row)[V], C (&L)[R], C (&Rt)[R]) {
 #pragma unroll
@@ -202,7 +199,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
             const int r = ib + PF + lane;
             int s = sb + PF + lane;
             if (s >= D) s -= D;
-            if (r < nrows) issue(r, s);
+            if (r < rend) issue(r, s);
         }
     };
     auto advance = [&]() {
@@ -217,7 +214,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
     auto drain = [&](int ib) {
         int s = sb;
         uint32_t ph = par;
-        for (int r = ib; r < ib + PF + P && r < nrows; ++r) {
+        for (int r = ib; r < ib + PF + P && r < rend; ++r) {
             if (!mbar_wait_warp(&bars[s], ph, status)) break;
             if (++s == D) {
                 s = 0;
@@ -231,9 +228,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
     // even x-shifts.  An odd x-shift would pair cells of two different
     // pairs, so those terms run as scalar fmas on the two halves of the
     // packed accumulator.  Each half still sees exactly the canonical chain.
-    constexpr bool PACKED = std::is_same<S, float>::value && MODE == MODE_PLAIN;
+    constexpr bool PACKED = PACK && std::is_same<S, float>::value && MODE == MODE_PLAIN;
     constexpr int H = V / 2;
-    const auto &cp = a.kp.c;
 
     if constexpr (SHAPE == SH_STAR && PACKED) {
         // rr[t][r % P][h] = cells 2h, 2h+1 of level-t row r, t = 0..bT-1
@@ -344,7 +340,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
                 ok = group(std::true_type{}, std::true_type{}, ib);
             if (!ok) {
                 drain(ib);
-                return;
+                return false;
             }
             advance();
         }
@@ -458,7 +454,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
                 ok = group(std::true_type{}, std::true_type{}, ib);
             if (!ok) {
                 drain(ib);
-                return;
+                return false;
             }
             advance();
         }
@@ -545,7 +541,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
                 ok = group(std::true_type{}, std::true_type{}, ib);
             if (!ok) {
                 drain(ib);
-                return;
+                return false;
             }
             advance();
         }
@@ -635,11 +631,41 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
                 ok = group(std::true_type{}, std::true_type{}, ib);
             if (!ok) {
                 drain(ib);
-                return;
+                return false;
             }
             advance();
         }
     }
+    return true;
+}
+
+template <int SHAPE, int R, int BT, typename S, int MODE>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE, BT, R, MODE>::value))
+    sweep2d_kernel(const __grid_constant__ CUtensorMap tmap,
+                   const Sweep2DArgs<S, NCoeff2<SHAPE, R>::value> a)
+{
+    using G = Sweep2DGeom<S, BT, R>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * WARPS_PER_CTA + warp;
+    if (gw >= a.total_warps) return;
+    // tile geometry (Section 3.1): tiles advance by the compute-region width,
+    // each starting bT*R cells left of its compute region
+    const int xt = gw % a.tiles_x;
+    const int sbk = gw / a.tiles_x;
+    Tile2D tg;
+    tg.pitch = a.pitch;
+    tg.ny = a.ny;
+    tg.nx = a.nx;
+    tg.x0 = R - BT * R + xt * a.tile_stride;
+    tg.sc0 = max(R, tg.x0 + BT * R);
+    tg.sc1 = min(a.nx + R, tg.x0 + BT * R + a.tile_stride);
+    tg.y0 = R + sbk * a.hsn;
+    tg.y1 = min(tg.y0 + a.hsn, a.ny + R);
+    unsigned char *const smem_al = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
+    sweep2d_tile<SHAPE, R, BT, S, MODE, true>(tg, &tmap, a.dst, a.status, smem_al + warp * G::WARP_BYTES,
+                                              a.k.c, a.kp.c);
 }
 
 // Host-side launcher of one instantiation.

@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
     const int zs = max(0, z0 - BT * R);
     const int ib0 = zs - zs % P;
     const int iend = z1 + BT * R;
+    const int pend = min(nplanes, iend);       // planes requested: exactly the planes consumed
 
     const int col0 = x0 + lane * V;
     const int row0 = yb + warp * RW;          // padded row of this warp's first row
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
     __syncthreads();
     if (warp == 0)
         for (int q = 0; q < PF; ++q)
-            if (ib0 + q < nplanes) issue_plane(ib0 + q, q);
+            if (ib0 + q < pend) issue_plane(ib0 + q, q);
 
     // Ring position of the current plane i: slot cs, mbarrier phase cpar.
     int cs = 0;
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
     // so that every CTA barrier of the group is still reached; the pass's
     // result is then discarded (the plan's status reports the timeout).
     auto load_plane = [&](int i, bool have, C (&cell)[RW][V], bool &ok) {
-        if (warp == 0 && ok && i + PF < nplanes) {
+        if (warp == 0 && ok && i + PF < pend) {
             int s = cs + PF;
             if (s >= D) s -= D;
             issue_plane(i + PF, s);
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
         if (fpl < 0) return;
         int s = fcs;
         uint32_t ph = fpar;
-        for (int p = fpl; p <= fpl + PF && p < nplanes; ++p) {
+        for (int p = fpl; p <= fpl + PF && p < pend; ++p) {
             if (!mbar_wait_warp(&bars[s], ph, status)) break;
             if (++s == D) {
                 s = 0;

@@ -1,0 +1,102 @@
+"""GPU parity of the batched form: every grid of a batch gets the bits of
+the single-grid method (the CPU oracle for small batches, the oracle-exact
+single-grid GPU path for the full 512-grid batch)."""
+import numpy as np
+import pytest
+
+from paper_2001_01473_gb300 import an5d, inputs
+from _gpu_util import assert_bitwise, oracle_run
+
+pytestmark = pytest.mark.gpu
+STAR, BOX = inputs.STAR, inputs.BOX
+
+
+def _grids_from(descs, seed0=100):
+    grids = []
+    for i, d in enumerate(descs):
+        n = inputs.coeff_count(2, d.shape, d.radius)
+        grids.append((d.shape, d.radius, inputs.normalised_coeffs(n, seed0 + i), d.ny, d.nx, d.T))
+    return grids
+
+
+def _inputs(grids, seed0=500):
+    import torch
+    xs = [torch.from_numpy(inputs.field((g[3], g[4]), g[1], seed0 + i, "f32")).cuda()
+          for i, g in enumerate(grids)]
+    return xs, [torch.empty_like(x) for x in xs]
+
+
+def _check_vs_oracle(grids, xs, ys):
+    for i, g in enumerate(grids):
+        shape, R, c, ny, nx, T = g
+        ref = oracle_run(2, shape, R, c, "f32", (ny, nx), xs[i].cpu().numpy(), T)
+        assert_bitwise(ys[i].cpu().numpy(), ref, f"grid {i} {g[:2]} {ny}x{nx} T={T}")
+
+
+SMALL = inputs.batch_descs(n=24, seed=7, side_lo=20, side_hi=400, t_lo=0, t_hi=40)
+
+
+@pytest.mark.parametrize("degrees", [None, (1, 1, 1, 1), (4, 2, 4, 2), (8, 4, 8, 4)])
+def test_batch_small_vs_oracle(degrees):
+    import torch
+    grids = _grids_from(SMALL)
+    with an5d.Batch(grids) as b:
+        if degrees:
+            b.set_degrees(degrees)
+        xs, ys = _inputs(grids)
+        b.run(xs, ys)
+        torch.cuda.synchronize()
+        assert b.status() == 0, an5d.an5d_batch_last_error()
+        _check_vs_oracle(grids, xs, ys)
+
+
+def test_batch_graph_replay_and_new_buffers():
+    import torch
+    grids = _grids_from(SMALL[:10])
+    with an5d.Batch(grids) as b:
+        xs, ys = _inputs(grids)
+        b.run(xs, ys)
+        b.run(xs, ys)                        # graph replay, same buffers
+        torch.cuda.synchronize()
+        assert b.status() == 0
+        _check_vs_oracle(grids, xs, ys)
+        xs2, ys2 = _inputs(grids, seed0=900)  # new buffers: table rebuilt
+        b.run(xs2, ys2)
+        torch.cuda.synchronize()
+        assert b.status() == 0
+        _check_vs_oracle(grids, xs2, ys2)
+
+
+def test_batch_rejects_bad_input():
+    with pytest.raises(an5d.An5dError):
+        an5d.Batch([(STAR, 3, np.ones(13), 10, 10, 5)])
+    import torch
+    grids = _grids_from(SMALL[:2])
+    with an5d.Batch(grids) as b:
+        xs, ys = _inputs(grids)
+        with pytest.raises(an5d.An5dError) as e:
+            b.run(xs, [xs[0], ys[1]])
+        assert e.value.status == an5d.AN5D_ERR_ALIAS
+
+
+def test_batch_full_config_vs_single_grid_path():
+    """512 grids, sides log-uniform in [128, 4096], star/box R1-2, T in [10, 500]:
+    every grid equal to the single-grid method's result, bit for bit."""
+    import torch
+    grids = _grids_from(inputs.batch_descs())
+    with an5d.Batch(grids) as b:
+        info = b.tune()
+        xs, ys = _inputs(grids)
+        b.run(xs, ys)
+        torch.cuda.synchronize()
+        assert b.status() == 0, an5d.an5d_batch_last_error()
+    bad = []
+    for i, g in enumerate(grids):
+        shape, R, c, ny, nx, T = g
+        with an5d.Plan(2, shape, R, c, "f32", (ny, nx)) as p:
+            ref = torch.empty_like(xs[i])
+            p.run(xs[i], ref, T)
+            torch.cuda.synchronize()
+        if not torch.equal(ref, ys[i]):
+            bad.append(i)
+    assert not bad, (bad[:10], info)
