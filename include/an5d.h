@@ -204,6 +204,22 @@ int an5d_run_noalloc(int ndim, an5d_shape shape, int radius, const double *coeff
 int an5d_error_norms(int ndim, int radius, const int64_t *dims, an5d_dtype dtype, const void *u,
                      const double *ref, double *out, void *stream);
 
+/* Adjoint (reverse-mode gradient) of an5d_run for 2D FP32 plans of radius
+ * 1-2.  For a loss L of u_T = S^T(u0):
+ *   u0        device, the forward input (padded FP32)
+ *   gT        device, dL/du_T (padded FP32; its halo is ignored)
+ *   grad_u0   device output, dL/du0 on the interior, 0 on the halo (the
+ *             halo is boundary data, not a parameter)
+ *   grad_coeffs host output, dL/dc_k, k in canonical order (FP64)
+ * g_t = S^T g_{t+1} is the transposed stencil (offsets -o_k, zero halo);
+ * dL/dc_k = sum_t sum_p g_{t+1}[p] u_t[p + o_k].  Checkpoints every bT
+ * steps (bT = min(plan degree, 4)); each block recomputes its states from
+ * its checkpoint and runs the transposed stencil over the block as one
+ * temporally blocked pass.  Allocates its work buffers (T/bT + 2 bT grids)
+ * per call; synchronous.  (No counterpart in the paper.) */
+int an5d_run_adjoint(an5d_plan *plan, const void *u0, const void *gT, void *grad_u0,
+                     double *grad_coeffs, int64_t T, void *stream);
+
 /* ------------------------------------------------------------------------
  * Batched form: many independent 2D FP32 grids of uneven size, stencil and
  * length in one persistent launch replayed as a CUDA graph.  (No counterpart

@@ -105,6 +105,8 @@ def load(path: str = LIB_PATH):
     L.an5d_run_noalloc.restype = I
     L.an5d_error_norms.argtypes = [I, I, P, I, P, P, P, P]
     L.an5d_error_norms.restype = I
+    L.an5d_run_adjoint.argtypes = [P, P, P, P, P, I64, P]
+    L.an5d_run_adjoint.restype = I
     L.an5d_batch_plan_create.argtypes = [I, P]
     L.an5d_batch_plan_create.restype = P
     L.an5d_batch_tune.argtypes = [P, P]
@@ -223,6 +225,14 @@ def an5d_error_norms(ndim: int, radius: int, dims, dtype, u, ref, stream=None) -
     return {"max_abs": float(out[0]), "l2_diff": float(np.sqrt(out[1])),
             "l2_ref": float(np.sqrt(out[2])),
             "rel_l2": float(np.sqrt(out[1] / out[2])) if out[2] > 0 else float("nan")}
+
+
+def an5d_run_adjoint(plan: int, u0, gT, grad_u0, T: int, stream=None) -> np.ndarray:
+    """Adjoint run (see an5d.h); returns dL/dc as a float64 array."""
+    gc = np.zeros(128, dtype=np.float64)
+    _check(load().an5d_run_adjoint(plan, _ptr(u0), _ptr(gT), _ptr(grad_u0), gc.ctypes.data,
+                                   int(T), _stream(stream)))
+    return gc
 
 
 def an5d_plan_destroy(plan: int) -> None:

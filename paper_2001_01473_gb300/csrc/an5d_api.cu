@@ -758,3 +758,68 @@ extern "C" int an5d_run_noalloc(int ndim, an5d_shape shape, int radius, const do
     if (h & STATUS_TIMEOUT) return fail(AN5D_ERR_TIMEOUT, "a bounded device wait gave up");
     return ok();
 }
+
+// ---------------------------------------------------------------------------
+// Internal accessors for the other translation units (adjoint).
+
+namespace an5d {
+
+int plan_view(const an5d_plan *p, PlanView *v)
+{
+    if (!p || !v) return fail(AN5D_ERR_INVALID_ARG, "NULL plan");
+    v->ndim = p->ndim;
+    v->shape = p->shape;
+    v->radius = p->radius;
+    v->dtype = p->dtype;
+    v->n = p->n;
+    v->bt = p->bt;
+    v->hsn = p->hsn;
+    v->device = p->device;
+    v->nz = p->nz;
+    v->ny = p->ny;
+    v->nx = p->nx;
+    v->total = p->total;
+    v->bytes = p->bytes;
+    v->coeffs = p->coeffs;
+    return AN5D_OK;
+}
+
+int plan_fill_pass(const an5d_plan *p, int bt, const void *src, void *dst, PassDesc *d)
+{
+    PassGeom g;
+    if (int s = pass_geometry(p, bt, p->hsn, &g)) return s;
+    memset(d, 0, sizeof(*d));
+    const int A = 16 / (int)elem_size(p->dtype);
+    if (int s = encode_row_map(&d->tmap, src, p->dtype, p->total, g.k->tile_x + A)) return s;
+    d->dst = dst;
+    d->status = p->d_status;
+    d->pitch = p->nx + 2 * p->radius;
+    d->plane = d->pitch * (p->ny + 2 * p->radius);
+    d->nz = (int)p->nz;
+    d->ny = (int)p->ny;
+    d->nx = (int)p->nx;
+    d->tile_stride_x = g.tile_stride_x;
+    d->tile_stride_y = g.tile_stride_y;
+    d->tiles_x = g.tiles_x;
+    d->tiles_y = g.tiles_y;
+    d->hsn = g.hsn;
+    d->stream_blocks = g.stream_blocks;
+    d->total_units = g.units;
+    d->ctas = g.ctas;
+    for (int k = 0; k < p->n; ++k) d->coeffs[k] = p->coeffs[k];
+    return AN5D_OK;
+}
+
+int plan_launch_pass(const an5d_plan *p, int bt, const void *src, void *dst, cudaStream_t st)
+{
+    return launch_pass(p, bt, src, dst, st);
+}
+
+int plan_launch_halo_copy(const an5d_plan *p, const void *src, void *dst, cudaStream_t st)
+{
+    return launch_halo_copy(p, src, dst, st);
+}
+
+int set_error(int status, const char *msg) { return fail(status, "%s", msg); }
+
+}  // namespace an5d

@@ -73,3 +73,23 @@ struct Registrar {
 const KernelEntry *find_kernel(const KernelKey &k);
 
 }  // namespace an5d
+
+struct an5d_plan;
+
+namespace an5d {
+
+// Read-only view of a plan for translation units other than the C-ABI one.
+struct PlanView {
+    int ndim, shape, radius, dtype, n, bt, hsn, device;
+    int64_t nz, ny, nx, total;
+    size_t bytes;
+    const double *coeffs;  // rounded to the compute precision
+};
+int plan_view(const an5d_plan *p, PlanView *v);
+// Pass descriptor (tensor map over src, geometry, coefficients) of degree bt.
+int plan_fill_pass(const an5d_plan *p, int bt, const void *src, void *dst, PassDesc *d);
+int plan_launch_pass(const an5d_plan *p, int bt, const void *src, void *dst, cudaStream_t st);
+int plan_launch_halo_copy(const an5d_plan *p, const void *src, void *dst, cudaStream_t st);
+int set_error(int status, const char *msg);
+
+}  // namespace an5d

@@ -106,11 +106,14 @@ struct Tile2D {
 // stores the level-BT rows [y0, y1) x [sc0, sc1).  The caller owns the
 // warp's shared-memory ring (Sweep2DGeom::WARP_BYTES, 128-byte aligned).
 // cf[k] are the coefficients, cp[k] the same as packed (c_k, c_k) pairs
-// (used when PACK).  Returns false if a bounded wait gave up.
-template <int SHAPE, int R, int BT, typename S, int MODE, bool PACK, typename CF, typename CP>
+// (used when PACK).  With LEVELS (scalar paths only) the intermediate levels
+// t = 1..BT-1 are stored as well, level t into lvl[t], over the same region.
+// Returns false if a bounded wait gave up.
+template <int SHAPE, int R, int BT, typename S, int MODE, bool PACK, typename CF, typename CP,
+          bool LEVELS = false>
 __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap *tmap, S *const dst,
                                              int *const status, unsigned char *const ring,
-                                             const CF &cf, const CP &cp)
+                                             const CF &cf, const CP &cp, S *const *lvl = nullptr)
 {
     using C = typename StorageTraits<S>::C;
     using G = Sweep2DGeom<S, BT, R>;
@@ -173,6 +176,11 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
             L[d - 1] = __shfl_up_sync(FULL_MASK, row[V - d], 1);
             Rt[d - 1] = __shfl_down_sync(FULL_MASK, row[d - 1], 1);
         }
+    };
+    auto store_row_to = [&](S *base, int j, const C (&res)[V]) {
+        S *out = base + (j * pitch + col0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) st_pred<S>(out + v, to_storage<S>(res[v]), store_bits, v);
     };
     auto store_row = [&](int j, const C (&res)[V]) {
         S *out = dst + (j * pitch + col0);
@@ -520,6 +528,7 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
                         }
 #pragma unroll
                         for (int v = 0; v < V; ++v) rr[t][sj][v] = res[v];
+                        if (LEVELS && j >= y0 && j < y1) store_row_to(lvl[t], j, res);
                     } else {
                         store_row(j, res);
                     }
@@ -612,6 +621,7 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
                         }
 #pragma unroll
                         for (int v = 0; v < V; ++v) in_row[v] = out_row[v];
+                        if (LEVELS && e >= y0 && e < y1) store_row_to(lvl[t], e, out_row);
                     } else if (!CHECK || (e >= y0 && e < y1)) {
                         store_row(e, out_row);
                     }
