@@ -520,7 +520,8 @@ def run_batch(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    descs = inputs.batch_descs()
+    descs = inputs.batch_descs(n=args.batch_n, side_hi=args.batch_side_hi, t_lo=args.batch_tlo,
+                               t_hi=args.batch_thi)
     grids = []
     for i, d in enumerate(descs):
         n = inputs.coeff_count(2, d.shape, d.radius)
@@ -569,6 +570,61 @@ def run_batch(args, rank, world, local):
     return 0
 
 
+def run_adjoint_bench(args, rank, world, local):
+    """Adjoint form on the batched workload: loss 0.5 ||u_T - target||^2 per
+    grid (target uniform [0,1) from seed 2), gradients w.r.t. u_0 and the
+    coefficients by the checkpointed adjoint; timed over all 512 grids."""
+    import torch
+    from paper_2001_01473_gb300 import an5d
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    descs = inputs.batch_descs()
+    grids, plans, xs, gts = [], [], [], []
+    for i, d in enumerate(descs):
+        n = inputs.coeff_count(2, d.shape, d.radius)
+        c = inputs.normalised_coeffs(n, 100 + i)
+        grids.append((d.shape, d.radius, c, d.ny, d.nx, d.T))
+    with an5d.Batch(grids) as b:
+        b.tune(stream)
+        for i, g in enumerate(grids):
+            xs.append(torch.from_numpy(inputs.field((g[3], g[4]), g[1], 500 + i, "f32")).to(dev))
+        ys = [torch.empty_like(x) for x in xs]
+        b.run(xs, ys, stream)
+        torch.cuda.synchronize()
+        assert b.status() == 0
+    for i, g in enumerate(grids):
+        R = g[1]
+        tg = torch.from_numpy(inputs.target_field((g[3], g[4]), R, 2, "f32")).to(dev)
+        gt = torch.zeros_like(ys[i])
+        gt[R:-R, R:-R] = ys[i][R:-R, R:-R] - tg[R:-R, R:-R]
+        gts.append(gt)
+        plans.append(an5d.Plan(2, g[0], R, g[2], "f32", (g[3], g[4])))
+    del ys
+    gus = [torch.empty_like(x) for x in xs]
+    cells = sum(float(g[3] * g[4] * g[5]) for g in grids)
+    times = []
+    for rep in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, g in enumerate(grids):
+            an5d.an5d_run_adjoint(plans[i].handle, xs[i], gts[i], gus[i], g[5], stream)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    t = min(times)
+    for p in plans:
+        p.close()
+    line = {"mode": "adjoint", "metric": "GCell-updates/s", "value": cells / t / 1e9,
+            "unit": "GCell-updates/s", "seconds_per_step": t, "steps": len(times),
+            "config": {"grids": len(grids), "cell_updates_per_step": cells,
+                       "loss": "0.5*||u_T - target||^2, target U[0,1) seed 2",
+                       "schedule": "checkpoint every bT (<= 4) steps; per block: blocked "
+                                   "recompute + blocked transposed pass + coefficient reduction"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -585,6 +641,11 @@ def main():
                     help="report the precision forms (throughput and error vs FP64)")
     ap.add_argument("--precision-workload", default=None, choices=sorted(PRECISION_WORKLOADS))
     ap.add_argument("--batch", action="store_true", help="report the batched form (512 grids)")
+    ap.add_argument("--adjoint", action="store_true", help="report the adjoint form (512 grids)")
+    ap.add_argument("--batch-n", type=int, default=512)
+    ap.add_argument("--batch-side-hi", type=int, default=4096)
+    ap.add_argument("--batch-tlo", type=int, default=10)
+    ap.add_argument("--batch-thi", type=int, default=500)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -595,6 +656,8 @@ def main():
         return run_precision(args, rank, world, local)
     if args.batch:
         return run_batch(args, rank, world, local)
+    if args.adjoint:
+        return run_adjoint_bench(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 

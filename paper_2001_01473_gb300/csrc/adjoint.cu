@@ -49,6 +49,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<float, S
     const int xt = gw % a.tiles_x;
     const int sbk = gw / a.tiles_x;
     Tile2D tg;
+    tg.src = nullptr;
+    tg.total = 0;
     tg.pitch = a.pitch;
     tg.ny = a.ny;
     tg.nx = a.nx;

@@ -79,7 +79,8 @@ __device__ __noinline__ bool batch_tile(const Tile2D tg, const CUtensorMap *map,
     Coeffs25 cf;
 #pragma unroll
     for (int k = 0; k < N; ++k) cf.c[k] = gc[k];
-    const bool ok = sweep2d_tile<SHAPE, R, BT, float, MODE_PLAIN, false>(tg, map, dst, status, ring, cf.c, cf.c);
+    const bool ok = sweep2d_tile<SHAPE, R, BT, float, MODE_PLAIN, false, decltype(cf.c), decltype(cf.c), false, true>(
+        tg, map, dst, status, ring, cf.c, cf.c);
     __syncwarp();
     if ((threadIdx.x & 31) == 0) {
         using G = Sweep2DGeom<float, BT, R>;
@@ -158,6 +159,8 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32)
         const int src = w.pass == 0 ? 0 : (((np - w.pass) % 2 == 0) ? 1 : 2);
         float *dst = g.buf[((np - 1 - w.pass) % 2 == 0) ? 1 : 2];
         Tile2D tg;
+        tg.src = g.buf[src];
+        tg.total = g.pitch * (g.ny + 2 * g.radius);
         tg.pitch = g.pitch;
         tg.ny = g.ny;
         tg.nx = g.nx;
@@ -297,13 +300,19 @@ static void batch_layout(an5d_batch_plan *bp)
         max_passes = std::max(max_passes, g.passes);
         bp->cell_updates += (double)d.ny * d.nx * d.T;
     }
+    // Pass-major; inside a pass, grouped by (class, degree) so that the warps
+    // running at the same time share the same code (each class and degree is
+    // a separate, fully unrolled instantiation).  An item's dependencies (the
+    // same grid, pass p - 1) come earlier in the queue.
     for (int p = 0; p < max_passes; ++p)
-        for (int i = 0; i < bp->n; ++i) {
-            const BatchGrid &g = bp->grids[i];
-            if (p >= g.passes) continue;
-            for (int sb = 0; sb < g.nsb; ++sb)
-                for (int xt = 0; xt < g.tiles_x; ++xt) bp->items.push_back(BatchItem{i, xt, sb, p});
-        }
+        for (int cls = 0; cls < BATCH_CLASSES; ++cls)
+            for (int full = 1; full >= 0; --full)
+                for (int i = 0; i < bp->n; ++i) {
+                    const BatchGrid &g = bp->grids[i];
+                    if (p >= g.passes || g.cls != cls || (p < g.full) != (full == 1)) continue;
+                    for (int sb = 0; sb < g.nsb; ++sb)
+                        for (int xt = 0; xt < g.tiles_x; ++xt) bp->items.push_back(BatchItem{i, xt, sb, p});
+                }
     bp->n_counters = counter;
 }
 

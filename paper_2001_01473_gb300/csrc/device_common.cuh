@@ -99,6 +99,17 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Non-tensor bulk copy of `bytes` (a multiple of 16) from 16-byte aligned
+// global memory to 16-byte aligned shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ int pmod(int a, int m)
 {
     int r = a % m;

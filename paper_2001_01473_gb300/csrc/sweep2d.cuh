@@ -94,6 +94,8 @@ template <typename S, int SHAPE, int BT, int R, int MODE> struct Sweep2DOccupanc
 
 // Geometry of one warp tile of one pass.
 struct Tile2D {
+    const void *src;  // source array (RAW row copies only)
+    int total;        // elements of the source array (RAW row copies only)
     int pitch;     // padded row length nx + 2R (elements)
     int ny, nx;    // interior extents
     int x0;        // padded column of the tile's first cell
@@ -108,9 +110,12 @@ struct Tile2D {
 // cf[k] are the coefficients, cp[k] the same as packed (c_k, c_k) pairs
 // (used when PACK).  With LEVELS (scalar paths only) the intermediate levels
 // t = 1..BT-1 are stored as well, level t into lvl[t], over the same region.
-// Returns false if a bounded wait gave up.
+// With RAW the rows are fetched by non-tensor bulk copies from tg.src
+// (clamped to the array; the array's last partial 16-byte chunk by plain
+// loads) instead of through the tensor map: no descriptor to fetch, for
+// callers that switch arrays often.  Returns false if a bounded wait gave up.
 template <int SHAPE, int R, int BT, typename S, int MODE, bool PACK, typename CF, typename CP,
-          bool LEVELS = false>
+          bool LEVELS = false, bool RAW = false>
 __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap *tmap, S *const dst,
                                              int *const status, unsigned char *const ring,
                                              const CF &cf, const CP &cp, S *const *lvl = nullptr)
@@ -150,8 +155,23 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
     auto issue = [&](int r, int s) {
         const int lin = r * pitch + x0;
         fence_proxy_async();
-        mbar_expect_tx(&bars[s], G::ROWBUF * (int)sizeof(S));
-        tma_load_1d(ring + s * G::SLOT_BYTES, tmap, lin & ~(A - 1), &bars[s]);
+        if constexpr (!RAW) {
+            mbar_expect_tx(&bars[s], G::ROWBUF * (int)sizeof(S));
+            tma_load_1d(ring + s * G::SLOT_BYTES, tmap, lin & ~(A - 1), &bars[s]);
+        } else {
+            const int a0 = lin & ~(A - 1);             // window [a0, a0 + ROWBUF)
+            const int whole = tg.total & ~(A - 1);     // 16-byte chunks of the array
+            const int lo = max(a0, 0), hi = min(a0 + G::ROWBUF, whole);
+            S *slot = reinterpret_cast<S *>(ring + s * G::SLOT_BYTES);
+            const S *srcp = static_cast<const S *>(tg.src);
+            for (int e = max(lo, whole); e < min(a0 + G::ROWBUF, tg.total); ++e) slot[e - a0] = srcp[e];
+            if (hi > lo) {
+                mbar_expect_tx(&bars[s], (hi - lo) * (int)sizeof(S));
+                bulk_load(slot + (lo - a0), srcp + lo, (hi - lo) * (int)sizeof(S), &bars[s]);
+            } else {
+                mbar_expect_tx(&bars[s], 0);
+            }
+        }
     };
     auto row_in_slot = [&](int r, int s) -> const S * {
         return reinterpret_cast<const S *>(ring + s * G::SLOT_BYTES) + ((r * pitch + x0) & (A - 1)) +
@@ -664,6 +684,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
     const int xt = gw % a.tiles_x;
     const int sbk = gw / a.tiles_x;
     Tile2D tg;
+    tg.src = nullptr;
+    tg.total = 0;
     tg.pitch = a.pitch;
     tg.ny = a.ny;
     tg.nx = a.nx;
