@@ -161,6 +161,14 @@ int an5d_plan_set_config(an5d_plan *plan, int bT, int hsn);
  * are cached per (stencil, dtype, dims, device) for the process. */
 int an5d_plan_tune(an5d_plan *plan, int topk, int64_t T_probe, void *stream);
 
+/* Fault injection for tests of the failure path (2D plans): while enabled,
+ * warp 0 of every pass waits for 16 bytes that are never delivered.  The
+ * bounded wait gives up after about one second, the warp waits (bounded)
+ * for its real copies in flight and returns, and an5d_plan_status reports
+ * AN5D_ERR_TIMEOUT; the CUDA context stays usable.  Nothing traps or hangs.
+ * (No counterpart in the paper.) */
+int an5d_plan_inject_stall(an5d_plan *plan, int enable);
+
 /* Device-side status of the plan's finished work: AN5D_OK or
  * AN5D_ERR_TIMEOUT.  Synchronises the device.  Clears the status. */
 int an5d_plan_status(an5d_plan *plan);
@@ -270,6 +278,12 @@ int an5d_batch_run(an5d_batch_plan *bp, const void *const *ins, void *const *out
 int an5d_batch_status(an5d_batch_plan *bp);
 
 int an5d_batch_info(const an5d_batch_plan *bp, an5d_batch_info_t *info);
+
+/* Fault injection for tests: while enabled, the last work item waits for a
+ * pass count that is never reached; its bounded wait gives up after about
+ * one second, the batch aborts, and an5d_batch_status returns
+ * AN5D_ERR_TIMEOUT.  Nothing traps or hangs. */
+int an5d_batch_inject_stall(an5d_batch_plan *bp, int enable);
 const char *an5d_batch_last_error(void);
 void an5d_batch_plan_destroy(an5d_batch_plan *bp);
 

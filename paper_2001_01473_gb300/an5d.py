@@ -105,6 +105,10 @@ def load(path: str = LIB_PATH):
     L.an5d_run_noalloc.restype = I
     L.an5d_error_norms.argtypes = [I, I, P, I, P, P, P, P]
     L.an5d_error_norms.restype = I
+    L.an5d_plan_inject_stall.argtypes = [P, I]
+    L.an5d_plan_inject_stall.restype = I
+    L.an5d_batch_inject_stall.argtypes = [P, I]
+    L.an5d_batch_inject_stall.restype = I
     L.an5d_run_adjoint.argtypes = [P, P, P, P, P, I64, P]
     L.an5d_run_adjoint.restype = I
     L.an5d_batch_plan_create.argtypes = [I, P]
@@ -233,6 +237,14 @@ def an5d_run_adjoint(plan: int, u0, gT, grad_u0, T: int, stream=None) -> np.ndar
     _check(load().an5d_run_adjoint(plan, _ptr(u0), _ptr(gT), _ptr(grad_u0), gc.ctypes.data,
                                    int(T), _stream(stream)))
     return gc
+
+
+def an5d_plan_inject_stall(plan: int, enable: bool) -> int:
+    return _check(load().an5d_plan_inject_stall(plan, int(bool(enable))))
+
+
+def an5d_batch_inject_stall(bp: int, enable: bool) -> int:
+    return _bcheck(load().an5d_batch_inject_stall(bp, int(bool(enable))))
 
 
 def an5d_plan_destroy(plan: int) -> None:

@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<float, S
     tg.sc1 = min(a.nx + R, tg.x0 + BT * R + a.tile_stride);
     tg.y0 = R + sbk * a.hsn;
     tg.y1 = min(tg.y0 + a.hsn, a.ny + R);
+    tg.stall = 0;
     unsigned char *const smem_al = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
     sweep2d_tile<SHAPE, R, BT, float, MODE_PLAIN, false, decltype(a.k.c), decltype(a.k.c), true>(
@@ -166,6 +167,7 @@ cudaError_t launch_levels(const PassDesc &d, const LevelPtrs &lv, cudaStream_t s
     a.tiles_x = d.tiles_x;
     a.hsn = d.hsn;
     a.total_warps = d.total_units;
+    a.stall_test = 0;
     for (int k = 0; k < N; ++k) {
         a.k.c[k] = static_cast<float>(d.coeffs[k]);
         a.kp.c[k] = 0;

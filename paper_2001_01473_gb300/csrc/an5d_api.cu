@@ -158,6 +158,7 @@ struct an5d_plan {
     int hsn = 0;
     double model_gcells = 0, measured_gcells = 0;
     int bt_max = 0;
+    int stall_test = 0;  // fault injection (tests only)
 };
 
 extern "C" const char *an5d_version(void) { return "an5d-gb300 0.1 (sm_103a)"; }
@@ -459,6 +460,7 @@ static int launch_pass(const an5d_plan *p, int bt, const void *src, void *dst, c
     d.stream_blocks = g.stream_blocks;
     d.total_units = g.units;
     d.ctas = g.ctas;
+    d.stall_test = p->ndim == 2 ? p->stall_test : 0;
     for (int k = 0; k < p->n; ++k) d.coeffs[k] = p->coeffs[k];
     CUDA_TRY(g.k->launch(d, st));
     return AN5D_OK;
@@ -823,3 +825,11 @@ int plan_launch_halo_copy(const an5d_plan *p, const void *src, void *dst, cudaSt
 int set_error(int status, const char *msg) { return fail(status, "%s", msg); }
 
 }  // namespace an5d
+
+extern "C" int an5d_plan_inject_stall(an5d_plan *p, int enable)
+{
+    if (!p) return fail(AN5D_ERR_INVALID_ARG, "NULL plan");
+    if (p->ndim != 2) return fail(AN5D_ERR_UNSUPPORTED, "stall injection is built for 2D plans");
+    p->stall_test = enable ? 1 : 0;
+    return ok();
+}

@@ -36,6 +36,7 @@ struct PassDesc {
     int stream_blocks;
     int total_units;         // warps (2D) or CTAs (3D) that carry work
     int ctas;                // grid size
+    int stall_test;          // fault injection (tests only)
     double coeffs[MAX_COEFFS];
 };
 

@@ -111,7 +111,7 @@ __device__ __forceinline__ int ld_acquire(const int *p)
 
 __global__ void __launch_bounds__(BATCH_WARPS * 32)
     batch_kernel(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items, int n_items,
-                 int *queue, int *counters, int *status, int *abort_flag)
+                 int *queue, int *counters, int *status, int *abort_flag, int stall_item)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *const base = reinterpret_cast<unsigned char *>(
@@ -129,13 +129,15 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32)
         const BatchGrid &g = grids[w.g];
         // wait until the 3x3 neighbourhood has completed pass w.pass - 1
         bool ok = true;
-        if (w.pass > 0 && lane < 9) {
+        int need = w.pass;
+        if (stall_item == it) need = 1 << 30;  // fault injection (tests only): never satisfied
+        if (need > 0 && lane < 9) {
             const int xt = w.xt + lane % 3 - 1, sb = w.sb + lane / 3 - 1;
             if (xt >= 0 && xt < g.tiles_x && sb >= 0 && sb < g.nsb) {
                 const int *c = counters + g.counter_base + sb * g.tiles_x + xt;
-                if (ld_acquire(c) < w.pass) {
+                if (ld_acquire(c) < need) {
                     const uint64_t t0 = global_ns();
-                    while (ld_acquire(c) < w.pass) {
+                    while (ld_acquire(c) < need) {
                         if (global_ns() - t0 > WAIT_LIMIT_NS) {
                             ok = false;
                             break;
@@ -169,6 +171,7 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32)
         tg.sc1 = min(g.nx + g.radius, tg.x0 + g.lead + g.stride);
         tg.y0 = g.radius + w.sb * g.hsn;
         tg.y1 = min(tg.y0 + g.hsn, g.ny + g.radius);
+        tg.stall = 0;
         const CUtensorMap *map = &g.map[src];
         bool done;
         switch (g.cls) {
@@ -238,6 +241,7 @@ struct an5d_batch_plan {
     std::vector<const void *> last_in;
     std::vector<void *> last_out;
     double cell_updates = 0;
+    int stall_test = 0;                  // fault injection (tests only)
     std::string err;
 };
 
@@ -550,7 +554,8 @@ extern "C" int an5d_batch_run(an5d_batch_plan *bp, const void *const *ins, void 
         cudaMemsetAsync(bp->d_counters, 0, sizeof(int) * (bp->n_counters + 3), cs);
         batch_halo_kernel<<<dim3((maxrows + 7) / 8, bp->n), 256, 0, cs>>>(bp->d_grids);
         batch_kernel<<<bp->ctas, BATCH_WARPS * 32, BATCH_SMEM, cs>>>(bp->d_grids, bp->d_items, (int)bp->items.size(),
-                                                                   queue, bp->d_counters, queue + 2, queue + 1);
+                                                                   queue, bp->d_counters, queue + 2, queue + 1,
+                                                                   bp->stall_test ? (int)bp->items.size() - 1 : -1);
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = cudaGraphInstantiate(&bp->graph, g, 0);
         if (g) cudaGraphDestroy(g);
@@ -568,5 +573,16 @@ extern "C" int an5d_batch_status(an5d_batch_plan *bp)
     cudaMemcpy(h, bp->d_counters + bp->n_counters, sizeof(h), cudaMemcpyDeviceToHost);
     if (h[2] & STATUS_TIMEOUT) return bfail(AN5D_ERR_TIMEOUT, "a bounded device wait gave up");
     if (h[1]) return bfail(AN5D_ERR_TIMEOUT, "the batch was aborted");
+    return AN5D_OK;
+}
+
+extern "C" int an5d_batch_inject_stall(an5d_batch_plan *bp, int enable)
+{
+    if (!bp) return bfail(AN5D_ERR_INVALID_ARG, "NULL plan");
+    bp->stall_test = enable ? 1 : 0;
+    if (bp->graph) {               // the flag is a kernel argument: re-capture
+        cudaGraphExecDestroy(bp->graph);
+        bp->graph = nullptr;
+    }
     return AN5D_OK;
 }

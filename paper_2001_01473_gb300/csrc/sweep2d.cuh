@@ -51,6 +51,7 @@ template <typename S, int N> struct Sweep2DArgs {
     int tiles_x;
     int hsn;          // output rows per stream block
     int total_warps;  // tiles_x * stream blocks
+    int stall_test;   // fault injection (tests only): warp 0's first row never completes
     CoeffBlock<typename StorageTraits<S>::C, N> k;
     CoeffBlock<unsigned long long, N> kp;  // FP32: (c_k, c_k) packed pairs for f32x2 arithmetic
 };
@@ -101,6 +102,7 @@ struct Tile2D {
     int x0;        // padded column of the tile's first cell
     int sc0, sc1;  // columns stored by this tile: [sc0, sc1)
     int y0, y1;    // rows stored by this tile (its stream block): [y0, y1)
+    int stall;     // fault injection (tests only): the first row's wait cannot complete
 };
 
 // One warp advances one tile of one stream block by BT time levels: it
@@ -183,6 +185,8 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
         fence_mbar_init();
     }
     __syncwarp();
+    if (tg.stall && lane == 0 && ib0 < rend) mbar_expect_tx_only(&bars[0], 16);  // never delivered
+    __syncwarp();
     if (lane < PF && ib0 + lane < rend) issue(ib0 + lane, lane);  // rows ib0 .. ib0+PF-1
 
     // Ring position of the group that starts at row ib: slots sb .. sb+P-1,
@@ -243,7 +247,7 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
         int s = sb;
         uint32_t ph = par;
         for (int r = ib; r < ib + PF + P && r < rend; ++r) {
-            if (!mbar_wait_warp(&bars[s], ph, status)) break;
+            mbar_wait_warp(&bars[s], ph, status);
             if (++s == D) {
                 s = 0;
                 ph ^= 1u;
@@ -694,6 +698,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
     tg.sc1 = min(a.nx + R, tg.x0 + BT * R + a.tile_stride);
     tg.y0 = R + sbk * a.hsn;
     tg.y1 = min(tg.y0 + a.hsn, a.ny + R);
+    tg.stall = a.stall_test && gw == 0;
     unsigned char *const smem_al = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
     sweep2d_tile<SHAPE, R, BT, S, MODE, true>(tg, &tmap, a.dst, a.status, smem_al + warp * G::WARP_BYTES,
@@ -717,6 +722,7 @@ cudaError_t launch_sweep2d(const PassDesc &d, cudaStream_t st)
     a.tiles_x = d.tiles_x;
     a.hsn = d.hsn;
     a.total_warps = d.total_units;
+    a.stall_test = d.stall_test;
     for (int k = 0; k < N; ++k) {
         a.k.c[k] = static_cast<C>(d.coeffs[k]);
         const float f = static_cast<float>(d.coeffs[k]);
