@@ -259,10 +259,15 @@ def oracle_time(ndim, shape, R, dtype, dims, budget_s=12.0):
         else:
             oracle.run_f32(ndim, shape, R, c.astype(np.float32), dims, u0, T)
 
+    # per-step cost without the oracle's set-up copies: difference of two runs
     t0 = time.perf_counter()
     run(1)
     t1 = time.perf_counter() - t0
-    T = max(1, min(1000, int(budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    run(3)
+    t3 = time.perf_counter() - t0
+    per_step = max((t3 - t1) / 2.0, 1e-4)
+    T = max(1, min(1000, int(budget_s / per_step)))
     t0 = time.perf_counter()
     run(T)
     dt = time.perf_counter() - t0
