@@ -60,6 +60,7 @@ WORKLOADS = {
     # smaller grids for profiler captures (still larger than the 129 MB L2)
     "star2d1r-f32-8k": (2, STAR, 1, "f32", (8192, 8192), 100),
     "box2d2r-f32-8k": (2, BOX, 2, "f32", (8192, 8192), 100),
+    "star3d1r-f32-320": (3, STAR, 1, "f32", (320, 320, 320), 30),
 }
 DEFAULT_WORKLOAD = "star2d1r-f32"
 

@@ -223,8 +223,9 @@ int an5d_error_norms(int ndim, int radius, const int64_t *dims, an5d_dtype dtype
  * dL/dc_k = sum_t sum_p g_{t+1}[p] u_t[p + o_k].  Checkpoints every bT
  * steps (bT = min(plan degree, 4)); each block recomputes its states from
  * its checkpoint and runs the transposed stencil over the block as one
- * temporally blocked pass.  Allocates its work buffers (T/bT + 2 bT grids)
- * per call; synchronous.  (No counterpart in the paper.) */
+ * temporally blocked pass.  Its work memory (T/bT + 2 bT grids) is owned by
+ * the plan, grown on demand and reused; synchronous.  (No counterpart in the
+ * paper.) */
 int an5d_run_adjoint(an5d_plan *plan, const void *u0, const void *gT, void *grad_u0,
                      double *grad_coeffs, int64_t T, void *stream);
 

@@ -83,10 +83,20 @@ template <int SHAPE, int R> __host__ __device__ constexpr int off_dx(int k)
     return (k - 1) % 2 == 0 ? i : 0;
 }
 
-constexpr int CORR_BLOCKS = 2048;
+constexpr int CORR_BLOCKS = 2048;  // at most; a grid uses corr_blocks(cells) of them
 constexpr int CORR_THREADS = 256;
 
-// part[b * n + k] = sum over block b's cells of g[p] * u[p + o_k] (interior p).
+// Fixed partition of a grid's cells for the coefficient reduction: at least
+// 16 cells per thread, at most CORR_BLOCKS blocks.  Depends only on the grid.
+__host__ __device__ inline int corr_blocks(int64_t cells)
+{
+    const int64_t b = (cells + (int64_t)CORR_THREADS * 16 - 1) / ((int64_t)CORR_THREADS * 16);
+    return (int)(b < 1 ? 1 : (b > CORR_BLOCKS ? CORR_BLOCKS : b));
+}
+
+// part[b * n + k] += sum over block b's cells of g[p] * u[p + o_k] (interior p).
+// Each block owns its slots and launches on one stream are ordered, so the
+// accumulation over steps is deterministic.
 template <int SHAPE, int R>
 __global__ void __launch_bounds__(CORR_THREADS)
     corr_kernel(const float *__restrict__ g, const float *__restrict__ u, int ny, int nx, double *part)
@@ -98,7 +108,7 @@ __global__ void __launch_bounds__(CORR_THREADS)
 #pragma unroll
     for (int k = 0; k < N; ++k) acc[k] = 0.f;
     for (int64_t q = blockIdx.x * (int64_t)CORR_THREADS + threadIdx.x; q < cells;
-         q += (int64_t)CORR_BLOCKS * CORR_THREADS) {
+         q += (int64_t)gridDim.x * CORR_THREADS) {
         const int y = (int)(q / nx) + R, x = (int)(q % nx) + R;
         const int64_t p = (int64_t)y * pitch + x;
         const float gv = g[p];
@@ -114,19 +124,19 @@ __global__ void __launch_bounds__(CORR_THREADS)
             if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
             __syncthreads();
         }
-        if (threadIdx.x == 0) part[blockIdx.x * N + k] = red[0];
+        if (threadIdx.x == 0) part[blockIdx.x * N + k] += red[0];
         __syncthreads();
     }
 }
 
-// dc[k] += sum_b part[b * n + k], in block order.
-__global__ void corr_final(const double *__restrict__ part, int n, double *dc)
+// dc[k] = sum_b part[b * n + k], in block order.
+__global__ void corr_final(const double *__restrict__ part, int n, int blocks, double *dc)
 {
     const int k = threadIdx.x;
     if (k >= n) return;
     double s = 0.0;
-    for (int b = 0; b < CORR_BLOCKS; ++b) s += part[b * n + k];
-    dc[k] += s;
+    for (int b = 0; b < blocks; ++b) s += part[b * n + k];
+    dc[k] = s;
 }
 
 // dst := src on the interior, 0 on the halo.
@@ -184,7 +194,7 @@ cudaError_t launch_levels(const PassDesc &d, const LevelPtrs &lv, cudaStream_t s
 template <int SHAPE, int R>
 void launch_corr(const float *g, const float *u, int ny, int nx, double *part, cudaStream_t st)
 {
-    corr_kernel<SHAPE, R><<<CORR_BLOCKS, CORR_THREADS, 0, st>>>(g, u, ny, nx, part);
+    corr_kernel<SHAPE, R><<<corr_blocks((int64_t)ny * nx), CORR_THREADS, 0, st>>>(g, u, ny, nx, part);
 }
 
 template <int SHAPE, int R> LevelsLaunch levels_for(int bt)
@@ -219,21 +229,6 @@ int mirror_index(int shape, int R, int k)
     return 1 + 2 * (2 * R - 1 - j) + axis;
 }
 
-struct DevBuf {
-    std::vector<void *> ptrs;
-    ~DevBuf()
-    {
-        for (void *p : ptrs) cudaFree(p);
-    }
-    void *alloc(size_t n)
-    {
-        void *p = nullptr;
-        if (cudaMalloc(&p, n) != cudaSuccess) return nullptr;
-        ptrs.push_back(p);
-        return p;
-    }
-};
-
 }  // namespace
 
 extern "C" int an5d_run_adjoint(an5d_plan *plan, const void *u0, const void *gT, void *grad_u0,
@@ -252,19 +247,29 @@ extern "C" int an5d_run_adjoint(an5d_plan *plan, const void *u0, const void *gT,
     const int ny = (int)v.ny, nx = (int)v.nx;
     const int bt = std::max(1, std::min(v.bt, ADJ_MAX_BT));
     const int64_t M = (T + bt - 1) / bt;
-    DevBuf mem;
-    auto grid = [&]() { return mem.alloc(v.bytes); };
-    double *dc = static_cast<double *>(mem.alloc(sizeof(double) * (n + (size_t)CORR_BLOCKS * n)));
-    if (!dc) return set_error(AN5D_ERR_OOM, "adjoint: work buffers");
+    // one work allocation, owned and reused by the plan: checkpoints C[1..M-1],
+    // u levels U[1..bt-1], g levels G[0..bt], dc and the reduction partials
+    const size_t gbytes = (v.bytes + 255) / 256 * 256;
+    const size_t ngrids = (size_t)std::max<int64_t>(M - 1, 0) + (bt - 1) + (bt + 1);
+    char *work = static_cast<char *>(
+        plan_work_buffer(plan, ngrids * gbytes + sizeof(double) * (n + (size_t)CORR_BLOCKS * n)));
+    if (!work) return set_error(AN5D_ERR_OOM, "adjoint: work memory");
+    size_t next = 0;
+    auto grid = [&]() -> void * {
+        void *p = work + next;
+        next += gbytes;
+        return p;
+    };
+    double *dc = reinterpret_cast<double *>(work + ngrids * gbytes);
     double *part = dc + n;
-    cudaMemsetAsync(dc, 0, sizeof(double) * n, st);
+    cudaMemsetAsync(dc, 0, sizeof(double) * (n + (size_t)CORR_BLOCKS * n), st);
     std::vector<double> mc(n);
     for (int k = 0; k < n; ++k) mc[k] = v.coeffs[mirror_index(v.shape, R, k)];
 
     // gradient of the final state, zero on the halo
     std::vector<void *> G(bt + 1);
     for (int j = 0; j <= bt; ++j) {
-        if (!(G[j] = grid())) return set_error(AN5D_ERR_OOM, "adjoint: g levels");
+        G[j] = grid();
         cudaMemsetAsync(G[j], 0, v.bytes, st);
     }
     interior_copy_kernel<<<1024, 256, 0, st>>>((const float *)gT, (float *)G[0], ny, nx, R);
@@ -279,14 +284,13 @@ extern "C" int an5d_run_adjoint(an5d_plan *plan, const void *u0, const void *gT,
     C[0] = u0;
     for (int64_t m = 1; m < M; ++m) {
         void *b = grid();
-        if (!b) return set_error(AN5D_ERR_OOM, "adjoint: checkpoints");
         if (int s = plan_launch_halo_copy(plan, u0, b, st)) return s;
         if (int s = plan_launch_pass(plan, bt, C[m - 1], b, st)) return s;
         C[m] = b;
     }
     std::vector<void *> U(bt);
     for (int s2 = 1; s2 < bt; ++s2) {
-        if (!(U[s2] = grid())) return set_error(AN5D_ERR_OOM, "adjoint: u levels");
+        U[s2] = grid();
         if (int s = plan_launch_halo_copy(plan, u0, U[s2], st)) return s;
     }
     CorrLaunch corr = find_corr(v.shape, R);
@@ -317,10 +321,10 @@ extern "C" int an5d_run_adjoint(an5d_plan *plan, const void *u0, const void *gT,
         for (int s2 = 0; s2 < nb; ++s2) {
             const float *u = (const float *)(s2 == 0 ? C[m] : U[s2]);
             corr((const float *)G[nb - 1 - s2], u, ny, nx, part, st);
-            corr_final<<<1, 32, 0, st>>>(part, n, dc);
         }
         std::swap(G[0], G[nb]);
     }
+    corr_final<<<1, 32, 0, st>>>(part, n, corr_blocks((int64_t)ny * nx), dc);
     cudaMemcpyAsync(grad_u0, G[0], v.bytes, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(grad_coeffs, dc, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);

@@ -159,6 +159,8 @@ struct an5d_plan {
     double model_gcells = 0, measured_gcells = 0;
     int bt_max = 0;
     int stall_test = 0;  // fault injection (tests only)
+    void *work = nullptr;  // reusable work memory of the adjoint (grown on demand)
+    size_t work_bytes = 0;
 };
 
 extern "C" const char *an5d_version(void) { return "an5d-gb300 0.1 (sm_103a)"; }
@@ -372,6 +374,7 @@ extern "C" void an5d_plan_destroy(an5d_plan *p)
     cudaFree(p->d_status);
     cudaFree(p->stage_in);
     cudaFree(p->stage_out);
+    cudaFree(p->work);
     if (cur >= 0) cudaSetDevice(cur);
     delete p;
 }
@@ -823,6 +826,19 @@ int plan_launch_halo_copy(const an5d_plan *p, const void *src, void *dst, cudaSt
 }
 
 int set_error(int status, const char *msg) { return fail(status, "%s", msg); }
+
+void *plan_work_buffer(an5d_plan *p, size_t bytes)
+{
+    if (p->work_bytes < bytes) {
+        cudaDeviceSynchronize();  // the old buffer may still be in use by queued work
+        cudaFree(p->work);
+        p->work = nullptr;
+        p->work_bytes = 0;
+        if (cudaMalloc(&p->work, bytes) != cudaSuccess) return nullptr;
+        p->work_bytes = bytes;
+    }
+    return p->work;
+}
 
 }  // namespace an5d
 

@@ -92,5 +92,7 @@ int plan_fill_pass(const an5d_plan *p, int bt, const void *src, void *dst, PassD
 int plan_launch_pass(const an5d_plan *p, int bt, const void *src, void *dst, cudaStream_t st);
 int plan_launch_halo_copy(const an5d_plan *p, const void *src, void *dst, cudaStream_t st);
 int set_error(int status, const char *msg);
+// The plan's reusable work memory, at least `bytes` (grown on demand, owned by the plan).
+void *plan_work_buffer(an5d_plan *p, size_t bytes);
 
 }  // namespace an5d
