@@ -55,6 +55,11 @@ WORKLOADS = {
     "star3d3r-f32": (3, STAR, 3, "f32", (512, 512, 512), 200),
     "star3d4r-f32": (3, STAR, 4, "f32", (512, 512, 512), 200),
     "box3d1r-f32": (3, BOX, 1, "f32", (512, 512, 512), 200),
+    "box2d3r-f32": (2, BOX, 3, "f32", (16384, 16384), 1000),
+    "box2d4r-f32": (2, BOX, 4, "f32", (16384, 16384), 1000),
+    "box3d2r-f32": (3, BOX, 2, "f32", (512, 512, 512), 200),
+    "box3d3r-f32": (3, BOX, 3, "f32", (512, 512, 512), 200),
+    "box3d4r-f32": (3, BOX, 4, "f32", (512, 512, 512), 200),
     "star3d1r-f64": (3, STAR, 1, "f64", (512, 512, 512), 200),
     "box3d1r-f64": (3, BOX, 1, "f64", (512, 512, 512), 200),
     # smaller grids for profiler captures (still larger than the 129 MB L2)
@@ -70,12 +75,14 @@ PAPER_V100_GCELLS = {
     "star2d1r-f32": 5631 / 9, "star2d2r-f32": 6319 / 17, "star2d3r-f32": 7132 / 25,
     "star2d4r-f32": 7244 / 33, "box2d1r-f32": 6693 / 17, "box2d2r-f32": 9163 / 49,
     "star2d1r-f64": 3306 / 9, "star2d2r-f64": 3071 / 17, "box2d1r-f64": 2984 / 17,
+    "box2d3r-f32": 10227 / 97, "box2d4r-f32": 10772 / 161,
 }
 # Table 5's 3D rows are for 512^3 with 1000 iterations; this benchmark runs
 # the 512^3 grids for T = 200, so they are context, not the same workload.
 PAPER_V100_3D_CONTEXT = {
     "star3d1r-f32": 2887 / 13, "star3d2r-f32": 2910 / 25, "star3d3r-f32": 3118 / 37,
-    "star3d4r-f32": 2808 / 49, "box3d1r-f32": 6284 / 53,
+    "star3d4r-f32": 2808 / 49, "box3d1r-f32": 6284 / 53, "box3d2r-f32": 8666 / 249,
+    "box3d3r-f32": 9351 / 685, "box3d4r-f32": 9707 / 1457,
 }
 
 # GB300 unit counts and clock used for the ALU peak: 152 SMs x 128 FP32 lanes
@@ -407,7 +414,8 @@ def run_ours(args, rank, world, local):
                 "peak_source": (f"{peak_src} MEASURED_PEAKS.json hbm_gbs" if bound == "hbm" else
                                 ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if dtype != "f64"
                                  else "in-run FP64 fma microbenchmark")),
-                "kernel": f"sweep{ndim}d_kernel bT={bt}", "launches_per_step": passes,
+                "kernel": (f"box1_kernel bT={bt}" if ndim == 3 and shape == BOX and R >= 2
+                           else f"sweep{ndim}d_kernel bT={bt}"), "launches_per_step": passes,
                 "full_degree_launches": full_passes,
                 "algorithmic_bytes_per_launch": hbm_bytes_launch,
                 "algorithmic_flops_per_launch": flops_launch,

@@ -233,7 +233,7 @@ def an5d_error_norms(ndim: int, radius: int, dims, dtype, u, ref, stream=None) -
 
 def an5d_run_adjoint(plan: int, u0, gT, grad_u0, T: int, stream=None) -> np.ndarray:
     """Adjoint run (see an5d.h); returns dL/dc as a float64 array."""
-    gc = np.zeros(128, dtype=np.float64)
+    gc = np.zeros(729, dtype=np.float64)  # room for the largest stencil
     _check(load().an5d_run_adjoint(plan, _ptr(u0), _ptr(gT), _ptr(grad_u0), gc.ctypes.data,
                                    int(T), _stream(stream)))
     return gc

@@ -304,6 +304,10 @@ extern "C" an5d_plan *an5d_plan_create(int ndim, an5d_shape shape, int radius,
 {
     int n = an5d_coeff_count(ndim, shape, radius);
     if (n < 0) return nullptr;
+    if (n > MAX_COEFFS) {
+        fail(AN5D_ERR_UNSUPPORTED, "%d coefficients exceed the library's %d", n, MAX_COEFFS);
+        return nullptr;
+    }
     if (!coeffs || !dims) {
         fail(AN5D_ERR_INVALID_ARG, "coeffs and dims must not be NULL");
         return nullptr;
@@ -693,6 +697,8 @@ extern "C" int an5d_run_noalloc(int ndim, an5d_shape shape, int radius, const do
 {
     int n = an5d_coeff_count(ndim, shape, radius);
     if (n < 0) return n;
+    if (n > MAX_COEFFS)
+        return fail(AN5D_ERR_UNSUPPORTED, "%d coefficients exceed the library's %d", n, MAX_COEFFS);
     if (!coeffs || !dims) return fail(AN5D_ERR_INVALID_ARG, "coeffs and dims must not be NULL");
     if (dtype < AN5D_F32 || dtype > AN5D_F32_COMPENSATED)
         return fail(AN5D_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);

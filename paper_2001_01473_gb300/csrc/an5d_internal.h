@@ -13,7 +13,7 @@ namespace an5d {
 enum Dtype : int { DT_F32 = 0, DT_F64 = 1, DT_F16S = 2, DT_F32C = 3 };
 enum Shape : int { SH_STAR = 0, SH_BOX = 1 };
 
-constexpr int MAX_COEFFS = 128;
+constexpr int MAX_COEFFS = 729;  // (2R+1)^3 for the largest stencil, box3d radius 4
 
 // Bits of a plan's device status word.
 enum : int { STATUS_TIMEOUT = 1 };

@@ -26,6 +26,11 @@ KERNELS_2D = [
     (STAR, 4, range(1, 3), "double", "MODE_PLAIN", "DT_F64"),
     (BOX, 1, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
     (BOX, 2, range(1, 4), "double", "MODE_PLAIN", "DT_F64"),
+    # high-order box (radius 3-4): temporal blocking stops paying, bT 1-2
+    (BOX, 3, range(1, 3), "float", "MODE_PLAIN", "DT_F32"),
+    (BOX, 4, range(1, 2), "float", "MODE_PLAIN", "DT_F32"),
+    (BOX, 3, range(1, 2), "double", "MODE_PLAIN", "DT_F64"),
+    (BOX, 4, range(1, 2), "double", "MODE_PLAIN", "DT_F64"),
     # precision forms: binary16 storage, Dot2-compensated FP32
     (STAR, 1, range(1, 11), "__half", "MODE_PLAIN", "DT_F16S"),
     (BOX, 1, range(1, 11), "__half", "MODE_PLAIN", "DT_F16S"),
@@ -57,6 +62,18 @@ KERNELS_3D = [
 ]
 
 
+# One-level 3D box sweeps for radius 2-4 (sweep3d_box1.cuh): (radius, storage
+# type, dtype tag, warps per CTA, rows per warp).  Each runs at bT = 1.
+KERNELS_3D_BOX1 = [
+    (2, "float", "DT_F32", 16, 2),
+    (3, "float", "DT_F32", 12, 2),
+    (4, "float", "DT_F32", 12, 2),
+    (2, "double", "DT_F64", 16, 1),
+    (3, "double", "DT_F64", 16, 1),
+    (4, "double", "DT_F64", 16, 1),
+]
+
+
 def instantiations():
     """Yield (header, entry expression) for every kernel instantiation."""
     for shape, r, bts, s, mode, dt in KERNELS_2D:
@@ -65,3 +82,5 @@ def instantiations():
     for shape, r, bts, s, mode, dt, nw in KERNELS_3D:
         for bt in bts:
             yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, {mode}, {nw}>({dt})"
+    for r, s, dt, nw, rw in KERNELS_3D_BOX1:
+        yield "sweep3d_box1.cuh", f"entry_box1<{r}, {s}, {nw}, {rw}>({dt})"

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2001_01473_gb300 import an5d, inputs
-from paper_2001_01473_gb300.kernels import KERNELS_3D
+from paper_2001_01473_gb300.kernels import KERNELS_3D, KERNELS_3D_BOX1
 from _gpu_util import assert_bitwise, coeffs_for, gpu_run, oracle_run
 
 pytestmark = pytest.mark.gpu
@@ -15,6 +15,8 @@ SH = {"SH_STAR": STAR, "SH_BOX": BOX}
 BUILT = {}
 for _sh, _r, _bts, _s, _m, _dt, _nw in KERNELS_3D:
     BUILT.setdefault((SH[_sh], _r, DT[_dt]), []).extend(list(_bts))
+for _r, _s, _dt, _nw, _rw in KERNELS_3D_BOX1:
+    BUILT.setdefault((BOX, _r, DT[_dt]), []).append(1)
 CASES = [(shape, R, dt, bt) for (shape, R, dt), bts in sorted(BUILT.items()) for bt in bts]
 
 
