@@ -60,6 +60,10 @@ def lib():
             fn = getattr(L, name)
             fn.argtypes = [i32, i32, i32, P, P, P, P, i64]
             fn.restype = i32
+        L.oracle_run_div_f32.argtypes = [i32, i32, i32, P, ctypes.c_float, i32, P, P, P, i64]
+        L.oracle_run_div_f32.restype = i32
+        L.oracle_run_div_f64.argtypes = [i32, i32, i32, P, ctypes.c_double, i32, P, P, P, i64]
+        L.oracle_run_div_f64.restype = i32
         L.oracle_adjoint_f64.argtypes = [i32, i32, i32, P, P, P, P, i64, P, P, P]
         L.oracle_adjoint_f64.restype = i32
         L.oracle_offsets.argtypes = [i32, i32, i32, P]
@@ -139,6 +143,29 @@ def run_dot2(ndim, shape, radius, coeffs, dims, u, T):
     """Compensated (Dot2) FP32 method."""
     return _run(lib().oracle_run_dot2, ndim, shape, radius, coeffs, dims, u, T,
                 np.float32, np.float32)
+
+
+POST_DIV, POST_MUL_RCP = 1, 2
+
+
+def run_div(dtype, ndim, shape, radius, coeffs, divisor, post, dims, u, T):
+    """Division-type stencil (Table 4's j* rows): the plain chain, then per
+    step a division by `divisor` (post=POST_DIV) or a multiplication by its
+    reciprocal rounded to the dtype (post=POST_MUL_RCP).  dtype: "f32" or
+    "f64"; `divisor` is rounded to the dtype first."""
+    if dtype == "f32":
+        fn, t = lib().oracle_run_div_f32, np.float32
+    elif dtype == "f64":
+        fn, t = lib().oracle_run_div_f64, np.float64
+    else:
+        raise ValueError(dtype)
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=t))
+    u = np.ascontiguousarray(u, dtype=t)
+    out = np.empty_like(u)
+    d = _dims(dims)
+    _check(fn(ndim, shape, radius, _ptr(c), float(t(divisor)), int(post), _ptr(d), _ptr(u),
+              _ptr(out), int(T)), fn.__name__)
+    return out
 
 
 def run_periodic_f64(ndim, shape, radius, coeffs, dims, u, T):

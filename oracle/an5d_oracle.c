@@ -204,6 +204,72 @@ int oracle_run_f64(int ndim, int shape, int R, const double *c, const int64_t *d
 }
 
 /* ------------------------------------------------------------------------ */
+/* Division-type stencils (Table 4: j2d5pt, j2d9pt, j2d9pt-gol, j3d27pt): the
+ * weighted sum of a star or box stencil divided by a constant d at every
+ * step.  post = 1 divides (one IEEE division, correctly rounded); post = 2
+ * multiplies by r = 1/d, itself rounded once to the run's precision (the
+ * paper's remedy for slow division, Section 6, replaces "/N" by "*(1/N)").
+ * The two generally differ in the last bit.  The division or multiplication
+ * follows the complete chain of the point (the chain is the same as the
+ * plain method's).                                                          */
+
+int oracle_run_div_f32(int ndim, int shape, int R, const float *c, float d, int post,
+                       const int64_t *dims, const float *in, float *out, int64_t T)
+{
+    geom_t g;
+    if (geom_init(&g, ndim, shape, R, dims, 0) || T < 0 || (post != 1 && post != 2)) return -1;
+    const float r = 1.0f / d;
+    float *A = (float *)malloc(sizeof(float) * g.total);
+    float *B = (float *)malloc(sizeof(float) * g.total);
+    if (!A || !B) { free(A); free(B); return -5; }
+    memcpy(A, in, sizeof(float) * g.total);
+    memcpy(B, in, sizeof(float) * g.total);
+    for (int64_t t = 0; t < T; ++t) {
+        #pragma omp parallel for schedule(static)
+        for (int64_t zy = 0; zy < g.nz * g.ny; ++zy) {
+            int64_t z = zy / g.ny + g.pz, y = zy % g.ny + g.R;
+            int64_t row = z * g.sz + y * g.sy;
+            for (int64_t x = g.R; x < g.R + g.nx; ++x) {
+                const float s = chain_f32(A, row + x, c, &g);
+                B[row + x] = (post == 1) ? s / d : s * r;
+            }
+        }
+        float *tmp = A; A = B; B = tmp;
+    }
+    memcpy(out, A, sizeof(float) * g.total);
+    free(A); free(B);
+    return 0;
+}
+
+int oracle_run_div_f64(int ndim, int shape, int R, const double *c, double d, int post,
+                       const int64_t *dims, const double *in, double *out, int64_t T)
+{
+    geom_t g;
+    if (geom_init(&g, ndim, shape, R, dims, 0) || T < 0 || (post != 1 && post != 2)) return -1;
+    const double r = 1.0 / d;
+    double *A = (double *)malloc(sizeof(double) * g.total);
+    double *B = (double *)malloc(sizeof(double) * g.total);
+    if (!A || !B) { free(A); free(B); return -5; }
+    memcpy(A, in, sizeof(double) * g.total);
+    memcpy(B, in, sizeof(double) * g.total);
+    for (int64_t t = 0; t < T; ++t) {
+        #pragma omp parallel for schedule(static)
+        for (int64_t zy = 0; zy < g.nz * g.ny; ++zy) {
+            int64_t z = zy / g.ny + g.pz, y = zy % g.ny + g.R;
+            int64_t row = z * g.sz + y * g.sy;
+            for (int64_t x = g.R; x < g.R + g.nx; ++x) {
+                const double s = chain_f64(A, row + x, c, &g);
+                B[row + x] = (post == 1) ? s / d : s * r;
+            }
+        }
+        double *tmp = A; A = B; B = tmp;
+    }
+    memcpy(out, A, sizeof(double) * g.total);
+    free(A); free(B);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Periodic FP64 variant: no halo, every index wraps modulo the extent.
  * Used only for the plane-wave eigenvalue check (a Fourier mode of a
  * periodic linear stencil is multiplied by lambda = sum_k c_k e^{i theta.o_k}
