@@ -67,7 +67,31 @@ WORKLOADS = {
     "box2d2r-f32-8k": (2, BOX, 2, "f32", (8192, 8192), 100),
     "star3d1r-f32-320": (3, STAR, 1, "f32", (320, 320, 320), 30),
 }
+# Division-type stencils (Table 4's j* rows): the same chain divided every step
+# by DIVISOR, exactly ("div") or through the rounded reciprocal ("rcp"); the
+# coefficients are the normalised ones scaled by DIVISOR.
+DIVISOR = 7.0
+DIV_WORKLOADS = {
+    "j2d5pt-f32": (2, STAR, 1, "f32", (16384, 16384), 1000, "div"),
+    "j2d5pt-rcp-f32": (2, STAR, 1, "f32", (16384, 16384), 1000, "rcp"),
+    "j2d9pt-f32": (2, STAR, 2, "f32", (16384, 16384), 1000, "div"),
+    "j2d9pt-gol-f32": (2, BOX, 1, "f32", (16384, 16384), 1000, "div"),
+    "j3d27pt-f32": (3, BOX, 1, "f32", (512, 512, 512), 200, "div"),
+    "j2d5pt-f64": (2, STAR, 1, "f64", (16384, 16384), 1000, "div"),
+}
 DEFAULT_WORKLOAD = "star2d1r-f32"
+
+
+def workload(name):
+    """(ndim, shape, R, dtype, dims, T, post); post is None for the plain method."""
+    if name in DIV_WORKLOADS:
+        return DIV_WORKLOADS[name]
+    return WORKLOADS[name] + (None,)
+
+
+def workload_coeffs(ndim, shape, R, post):
+    c = inputs.normalised_coeffs(inputs.coeff_count(ndim, shape, R), 0)
+    return c * DIVISOR if post else c
 
 # The paper's V100 SXM2 "Tuned" figures (Table 5) for the same stencil,
 # precision, grid and iteration count, in GCell/s (GFLOP/s / FLOP per cell).
@@ -76,13 +100,14 @@ PAPER_V100_GCELLS = {
     "star2d4r-f32": 7244 / 33, "box2d1r-f32": 6693 / 17, "box2d2r-f32": 9163 / 49,
     "star2d1r-f64": 3306 / 9, "star2d2r-f64": 3071 / 17, "box2d1r-f64": 2984 / 17,
     "box2d3r-f32": 10227 / 97, "box2d4r-f32": 10772 / 161,
+    "j2d5pt-f32": 6160 / 10, "j2d9pt-f32": 6398 / 18, "j2d9pt-gol-f32": 6865 / 18,
 }
 # Table 5's 3D rows are for 512^3 with 1000 iterations; this benchmark runs
 # the 512^3 grids for T = 200, so they are context, not the same workload.
 PAPER_V100_3D_CONTEXT = {
     "star3d1r-f32": 2887 / 13, "star3d2r-f32": 2910 / 25, "star3d3r-f32": 3118 / 37,
     "star3d4r-f32": 2808 / 49, "box3d1r-f32": 6284 / 53, "box3d2r-f32": 8666 / 249,
-    "box3d3r-f32": 9351 / 685, "box3d4r-f32": 9707 / 1457,
+    "box3d3r-f32": 9351 / 685, "box3d4r-f32": 9707 / 1457, "j3d27pt-f32": 6251 / 54,
 }
 
 # GB300 unit counts and clock used for the ALU peak: 152 SMs x 128 FP32 lanes
@@ -97,13 +122,14 @@ def bytes_per_cell(dtype: str) -> int:
     return {"f32": 4, "f64": 8, "f16": 2, "f32c": 4}[dtype]
 
 
-def flops_per_cell(ndim: int, shape: int, R: int, dtype: str) -> int:
+def flops_per_cell(ndim: int, shape: int, R: int, dtype: str, post=None) -> int:
     """Algorithmic flops of one cell-update: one multiply + (n-1) fma = 2n-1
-    (Table 4).  The compensated form counts Dot2's 10 flops per term."""
+    (Table 4), plus one for a division-type stencil's division.  The
+    compensated form counts Dot2's 10 flops per term."""
     n = inputs.coeff_count(ndim, shape, R)
     if dtype == "f32c":
         return 10 * n - 8
-    return 2 * n - 1
+    return 2 * n - 1 + (1 if post else 0)
 
 
 def load_measured_peaks():
@@ -248,17 +274,20 @@ def committed_traffic(workload: str, bt: int):
 # ---------------------------------------------------------------------------
 # Reference arm: the CPU oracle.
 
-def oracle_time(ndim, shape, R, dtype, dims, budget_s=12.0):
+def oracle_time(ndim, shape, R, dtype, dims, budget_s=12.0, post=None):
     """Time the oracle on a bounded sample of the workload: the full grid for
     a number of steps chosen so that the run takes about budget_s."""
     import oracle
-    n = inputs.coeff_count(ndim, shape, R)
-    c = inputs.normalised_coeffs(n, 0)
+    c = workload_coeffs(ndim, shape, R, post)
     u0 = inputs.field(dims, R, 1, dtype)
     cells = float(np.prod(dims))
 
     def run(T):
-        if dtype == "f64":
+        if post:
+            t = np.float64 if dtype == "f64" else np.float32
+            oracle.run_div(dtype, ndim, shape, R, c.astype(t), DIVISOR,
+                           oracle.POST_DIV if post == "div" else oracle.POST_MUL_RCP, dims, u0, T)
+        elif dtype == "f64":
             oracle.run_f64(ndim, shape, R, c, dims, u0, T)
         elif dtype == "f16":
             oracle.run_f16s(ndim, shape, R, c.astype(np.float32), dims, u0, T)
@@ -288,12 +317,13 @@ def oracle_time(ndim, shape, R, dtype, dims, budget_s=12.0):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    ndim, shape, R, dtype, dims, T = WORKLOADS[args.workload]
+    ndim, shape, R, dtype, dims, T, post = workload(args.workload)
     # each step is a bounded sample: the whole run stays within a few minutes
     budget = max(2.0, min(args.ref_budget, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(max(0, args.warmup)):
-        oracle_time(ndim, shape, R, dtype, dims, budget_s=min(budget, 2.0))
-    steps = [oracle_time(ndim, shape, R, dtype, dims, budget_s=budget) for _ in range(args.steps)]
+        oracle_time(ndim, shape, R, dtype, dims, budget_s=min(budget, 2.0), post=post)
+    steps = [oracle_time(ndim, shape, R, dtype, dims, budget_s=budget, post=post)
+             for _ in range(args.steps)]
     v = statistics.mean(s["value"] for s in steps)
     cpu = dict(steps[0])
     cpu["value"] = v
@@ -312,10 +342,15 @@ def run_reference(args, rank, world):
 
 
 def workload_config(name, world):
-    ndim, shape, R, dtype, dims, T = WORKLOADS[name]
+    ndim, shape, R, dtype, dims, T, post = workload(name)
+    div = ""
+    if post:
+        div = (f", divided by {DIVISOR:g} every step "
+               f"({'IEEE division' if post == 'div' else 'product with the rounded reciprocal'}; "
+               f"coefficients scaled by {DIVISOR:g})")
     return {"workload": f"{name}: {'star' if shape == STAR else 'box'} radius {R}, "
                         f"{'x'.join(map(str, dims))} interior + {R}-cell Dirichlet halo, T={T}, "
-                        f"seeded normalised coefficients, uniform [0,1) field",
+                        f"seeded normalised coefficients, uniform [0,1) field{div}",
             "stencil": name, "dims": list(dims), "T": T, "radius": R,
             "parallelism": f"replicas{world}" if world > 1 else "single",
             "l2": "inputs larger than L2 (1 GiB+ per buffer vs 129 MB)"}
@@ -331,15 +366,17 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist = dist_init(world, "nccl")
-    ndim, shape, R, dtype, dims, T = WORKLOADS[args.workload]
-    n = inputs.coeff_count(ndim, shape, R)
-    c = inputs.normalised_coeffs(n, 0)
+    ndim, shape, R, dtype, dims, T, post = workload(args.workload)
+    c = workload_coeffs(ndim, shape, R, post)
     u0 = inputs.field(dims, R, 1, dtype)
     cells = float(np.prod(dims))
     stream = torch.cuda.current_stream()
 
     inrun = an5d.an5d_measure_peaks(stream)        # copy / fma / smem microbenchmarks
-    plan = an5d.Plan(ndim, shape, R, c, dtype, dims)
+    if post:
+        plan = an5d.Plan(ndim, shape, R, c, dtype, dims, divisor=DIVISOR, post=post)
+    else:
+        plan = an5d.Plan(ndim, shape, R, c, dtype, dims)
     plan.tune(topk=args.topk, T_probe=args.tune_T, stream=stream)
     cfg = plan.config()
     bt = cfg["bT"]
@@ -397,7 +434,7 @@ def run_ours(args, rank, world, local):
     launch_s = ms_step * 1e-3 / passes            # halo copy (~us) included: conservative
     full_passes = T // bt
     hbm_bytes_launch = cells * 2 * w              # read once + write once per pass
-    flops_launch = cells * bt * flops_per_cell(ndim, shape, R, dtype)
+    flops_launch = cells * bt * flops_per_cell(ndim, shape, R, dtype, post)
     hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     alu_fp32 = NOMINAL_SMS * NOMINAL_FP32_LANES * 2 * NOMINAL_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
     alu_peak = alu_fp32 if dtype != "f64" else inrun["fp64_gflops"] / 1e3
@@ -442,7 +479,8 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_time(ndim, shape, R, dtype, dims, budget_s=args.ref_budget)
+        line["cpu_baseline"] = oracle_time(ndim, shape, R, dtype, dims, budget_s=args.ref_budget,
+                                            post=post)
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -645,7 +683,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(WORKLOADS) + sorted(DIV_WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--topk", type=int, default=6)
     ap.add_argument("--tune-T", type=int, default=40)

@@ -112,7 +112,7 @@ int an5d_coeff_count(int ndim, an5d_shape shape, int radius);
 /* Create a plan for one stencil on one grid size (Section 3.3 host code).
  *   ndim    2 or 3
  *   shape   AN5D_STAR or AN5D_BOX
- *   radius  1..4 for star; 1..2 for 2D box; 1 for 3D box
+ *   radius  1..4 (star, and box in 2D and 3D; high-order boxes run at bT 1-2)
  *   coeffs  host array of an5d_coeff_count(...) doubles in canonical order,
  *           rounded once to the run's compute precision here
  *   dtype   see an5d_dtype
@@ -123,6 +123,27 @@ int an5d_coeff_count(int ndim, an5d_shape shape, int radius);
  * on the current device.  Returns NULL on failure. */
 an5d_plan *an5d_plan_create(int ndim, an5d_shape shape, int radius, const double *coeffs,
                             an5d_dtype dtype, const int64_t *dims);
+
+/* Per-step operation of a division-type stencil (Table 4: j2d5pt, j2d9pt,
+ * j2d9pt-gol, j3d27pt divide the weighted sum by a constant c0 every step).
+ *   AN5D_POST_DIV      one IEEE division by the divisor (correctly rounded)
+ *   AN5D_POST_MUL_RCP  one multiplication by the divisor's reciprocal, itself
+ *                      rounded once to the compute precision (Section 6's
+ *                      remedy for slow division: "/N" becomes "*(1/N)") */
+typedef enum { AN5D_POST_DIV = 1, AN5D_POST_MUL_RCP = 2 } an5d_post;
+
+/* Create a plan for a division-type stencil: every step computes the plain
+ * chain of an5d_plan_create's stencil and then applies `post` with
+ * `divisor` (rounded once to the compute precision).  Same arguments,
+ * ownership and errors as an5d_plan_create, plus:
+ *   divisor  finite and nonzero, with a nonzero finite reciprocal
+ *   post     AN5D_POST_DIV or AN5D_POST_MUL_RCP
+ *   dtype    AN5D_F32 or AN5D_F64 (AN5D_ERR_UNSUPPORTED otherwise)
+ * Built: 2D star radius 1-2, 2D box radius 1, 3D box radius 1 (Table 4's
+ * division-type rows).  an5d_run_adjoint rejects these plans. */
+an5d_plan *an5d_plan_create_div(int ndim, an5d_shape shape, int radius, const double *coeffs,
+                                double divisor, an5d_post post, an5d_dtype dtype,
+                                const int64_t *dims);
 
 /* Advance T time steps: out = S^T(in).
  *   in, out  device pointers to padded arrays of the storage type

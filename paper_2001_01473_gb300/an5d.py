@@ -87,6 +87,8 @@ def load(path: str = LIB_PATH):
     L.an5d_coeff_count.restype = I
     L.an5d_plan_create.argtypes = [I, I, I, P, I, P]
     L.an5d_plan_create.restype = P
+    L.an5d_plan_create_div.argtypes = [I, I, I, P, ctypes.c_double, I, I, P]
+    L.an5d_plan_create_div.restype = P
     L.an5d_run.argtypes = [P, P, P, I64, P]
     L.an5d_run.restype = I
     L.an5d_run_host.argtypes = [P, P, P, I64, P]
@@ -281,17 +283,42 @@ def an5d_get_peaks() -> dict:
     return pk.as_dict()
 
 
+POST_DIV, POST_MUL_RCP = 1, 2
+POSTS = {"div": POST_DIV, "rcp": POST_MUL_RCP}
+
+
+def an5d_plan_create_div(ndim: int, shape: int, radius: int, coeffs, divisor: float, post,
+                         dtype, dims) -> int:
+    """Plan of a division-type stencil (see an5d.h); post: "div"/"rcp" or the enum value."""
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    pv = POSTS[post] if isinstance(post, str) else int(post)
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int64))
+    h = load().an5d_plan_create_div(ndim, shape, radius, c.ctypes.data, float(divisor), pv, dt,
+                                    d.ctypes.data)
+    if not h:
+        raise An5dError(an5d_last_status(), an5d_last_error())
+    return h
+
+
 # ---------------------------------------------------------------------------
 # Convenience wrapper.
 
 class Plan:
     """RAII wrapper of an an5d plan."""
 
-    def __init__(self, ndim: int, shape: int, radius: int, coeffs, dtype, dims):
+    def __init__(self, ndim: int, shape: int, radius: int, coeffs, dtype, dims,
+                 divisor=None, post=None):
+        """With `divisor` and `post` ("div" or "rcp") the plan is a
+        division-type stencil (an5d_plan_create_div)."""
         self.ndim, self.shape, self.radius = ndim, shape, radius
         self.dtype = dtype
         self.dims = tuple(int(d) for d in dims)
-        self.handle = an5d_plan_create(ndim, shape, radius, coeffs, dtype, dims)
+        if divisor is None:
+            self.handle = an5d_plan_create(ndim, shape, radius, coeffs, dtype, dims)
+        else:
+            self.handle = an5d_plan_create_div(ndim, shape, radius, coeffs, divisor,
+                                               post or "div", dtype, dims)
 
     def run(self, inp, out, T: int, stream=None) -> None:
         an5d_run(self.handle, inp, out, T, stream)

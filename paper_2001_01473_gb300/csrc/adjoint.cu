@@ -236,8 +236,9 @@ extern "C" int an5d_run_adjoint(an5d_plan *plan, const void *u0, const void *gT,
 {
     PlanView v;
     if (int s = plan_view(plan, &v)) return s;
-    if (v.ndim != 2 || v.dtype != AN5D_F32 || v.radius > 2)
-        return set_error(AN5D_ERR_UNSUPPORTED, "adjoint: 2D FP32 plans of radius 1-2 only");
+    if (v.ndim != 2 || v.dtype != AN5D_F32 || v.radius > 2 || v.post != POST_NONE)
+        return set_error(AN5D_ERR_UNSUPPORTED,
+                         "adjoint: 2D FP32 plans of radius 1-2 without a per-step division only");
     if (!u0 || !gT || !grad_u0 || !grad_coeffs || T < 0)
         return set_error(AN5D_ERR_INVALID_ARG, "adjoint: NULL argument or T < 0");
     if ((((uintptr_t)u0) | ((uintptr_t)gT) | ((uintptr_t)grad_u0)) & 15)

@@ -149,6 +149,8 @@ struct an5d_plan {
     size_t bytes;         // padded bytes
     int n;                // coefficients
     double coeffs[MAX_COEFFS];  // rounded to the compute precision
+    int post = POST_NONE; // per-step division (division-type stencils)
+    double post_c = 0;    // divisor or reciprocal, rounded to the compute precision
     int device;
     int sms;
     void *scratch = nullptr;
@@ -185,7 +187,7 @@ static int largest_bt(const an5d_plan *p)
     int best = 0;
     for (const auto &e : registry())
         if (e.key.ndim == p->ndim && e.key.shape == p->shape && e.key.radius == p->radius &&
-            e.key.dtype == p->dtype)
+            e.key.dtype == p->dtype && e.key.post == p->post)
             best = std::max(best, e.key.bt);
     return best;
 }
@@ -198,7 +200,7 @@ struct PassGeom {
 
 static int pass_geometry(const an5d_plan *p, int bt, int hsn_req, PassGeom *g)
 {
-    g->k = find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt});
+    g->k = find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post});
     if (!g->k)
         return fail(AN5D_ERR_UNSUPPORTED, "no kernel for ndim=%d shape=%d R=%d dtype=%d bT=%d",
                     p->ndim, p->shape, p->radius, p->dtype, bt);
@@ -283,7 +285,7 @@ static void choose_default(an5d_plan *p)
     double best = -1.0;
     int bbt = 1, bh = 0;
     for (int bt = 1; bt <= p->bt_max; ++bt) {
-        if (!find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt})) continue;
+        if (!find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post})) continue;
         const int h = default_hsn(p, bt, 1);
         const double m = model_for(p, bt, h);
         if (m > best) {
@@ -298,9 +300,8 @@ static void choose_default(an5d_plan *p)
     p->measured_gcells = 0.0;
 }
 
-extern "C" an5d_plan *an5d_plan_create(int ndim, an5d_shape shape, int radius,
-                                       const double *coeffs, an5d_dtype dtype,
-                                       const int64_t *dims)
+static an5d_plan *plan_create_impl(int ndim, an5d_shape shape, int radius, const double *coeffs,
+                                   an5d_dtype dtype, const int64_t *dims, int post, double post_c)
 {
     int n = an5d_coeff_count(ndim, shape, radius);
     if (n < 0) return nullptr;
@@ -342,10 +343,12 @@ extern "C" an5d_plan *an5d_plan_create(int ndim, an5d_shape shape, int radius,
     p->bytes = (size_t)total * elem_size(dtype);
     const bool dbl = dtype == AN5D_F64;
     for (int k = 0; k < n; ++k) p->coeffs[k] = dbl ? coeffs[k] : (double)(float)coeffs[k];
+    p->post = post;
+    p->post_c = post_c;
     p->bt_max = largest_bt(p);
     if (p->bt_max == 0) {
-        fail(AN5D_ERR_UNSUPPORTED, "stencil ndim=%d shape=%d R=%d dtype=%d is not built", ndim,
-             (int)shape, radius, (int)dtype);
+        fail(AN5D_ERR_UNSUPPORTED, "stencil ndim=%d shape=%d R=%d dtype=%d post=%d is not built",
+             ndim, (int)shape, radius, (int)dtype, post);
         delete p;
         return nullptr;
     }
@@ -365,6 +368,41 @@ extern "C" an5d_plan *an5d_plan_create(int ndim, an5d_shape shape, int radius,
     choose_default(p);
     ok();
     return p;
+}
+
+extern "C" an5d_plan *an5d_plan_create(int ndim, an5d_shape shape, int radius,
+                                       const double *coeffs, an5d_dtype dtype,
+                                       const int64_t *dims)
+{
+    return plan_create_impl(ndim, shape, radius, coeffs, dtype, dims, POST_NONE, 0.0);
+}
+
+extern "C" an5d_plan *an5d_plan_create_div(int ndim, an5d_shape shape, int radius,
+                                           const double *coeffs, double divisor, an5d_post post,
+                                           an5d_dtype dtype, const int64_t *dims)
+{
+    if (post != AN5D_POST_DIV && post != AN5D_POST_MUL_RCP) {
+        fail(AN5D_ERR_INVALID_ARG, "post must be AN5D_POST_DIV or AN5D_POST_MUL_RCP");
+        return nullptr;
+    }
+    if (dtype != AN5D_F32 && dtype != AN5D_F64) {
+        fail(AN5D_ERR_UNSUPPORTED, "division-type stencils are built for FP32 and FP64 only");
+        return nullptr;
+    }
+    // the divisor and its reciprocal, each rounded once to the compute precision
+    double c;
+    if (dtype == AN5D_F32) {
+        const float d = (float)divisor;
+        c = post == AN5D_POST_DIV ? (double)d : (double)(1.0f / d);
+    } else {
+        c = post == AN5D_POST_DIV ? divisor : 1.0 / divisor;
+    }
+    if (!std::isfinite(divisor) || divisor == 0.0 || !std::isfinite(c) || c == 0.0) {
+        fail(AN5D_ERR_INVALID_ARG, "divisor must be finite and nonzero, with a nonzero reciprocal");
+        return nullptr;
+    }
+    return plan_create_impl(ndim, shape, radius, coeffs, dtype, dims,
+                            post == AN5D_POST_DIV ? POST_DIV : POST_MUL, c);
 }
 
 extern "C" void an5d_plan_destroy(an5d_plan *p)
@@ -406,7 +444,7 @@ extern "C" int an5d_plan_set_config(an5d_plan *p, int bt, int hsn)
     if (!p) return fail(AN5D_ERR_INVALID_ARG, "NULL plan");
     if (bt < 0 || hsn < 0) return fail(AN5D_ERR_INVALID_ARG, "bT and hsn must be >= 0");
     const int nbt = bt > 0 ? bt : p->bt;
-    if (!find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, nbt}))
+    if (!find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, nbt, p->post}))
         return fail(AN5D_ERR_UNSUPPORTED, "bT=%d is not built for this stencil", nbt);
     p->bt = nbt;
     p->hsn = hsn > 0 ? hsn : default_hsn(p, nbt, 1);
@@ -468,6 +506,7 @@ static int launch_pass(const an5d_plan *p, int bt, const void *src, void *dst, c
     d.total_units = g.units;
     d.ctas = g.ctas;
     d.stall_test = p->ndim == 2 ? p->stall_test : 0;
+    d.post_c = p->post_c;
     for (int k = 0; k < p->n; ++k) d.coeffs[k] = p->coeffs[k];
     CUDA_TRY(g.k->launch(d, st));
     return AN5D_OK;
@@ -587,7 +626,7 @@ extern "C" int an5d_plan_tune(an5d_plan *p, int topk, int64_t T_probe, void *str
     };
     std::vector<Cand> cands;
     for (int bt = 1; bt <= p->bt_max; ++bt) {
-        if (!find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt})) continue;
+        if (!find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post})) continue;
         for (int waves = 1; waves <= 4; waves *= 2) {
             const int h = default_hsn(p, bt, waves);
             if (h <= 0) continue;
@@ -782,6 +821,7 @@ int plan_view(const an5d_plan *p, PlanView *v)
     v->shape = p->shape;
     v->radius = p->radius;
     v->dtype = p->dtype;
+    v->post = p->post;
     v->n = p->n;
     v->bt = p->bt;
     v->hsn = p->hsn;
@@ -817,6 +857,7 @@ int plan_fill_pass(const an5d_plan *p, int bt, const void *src, void *dst, PassD
     d->stream_blocks = g.stream_blocks;
     d->total_units = g.units;
     d->ctas = g.ctas;
+    d->post_c = p->post_c;
     for (int k = 0; k < p->n; ++k) d->coeffs[k] = p->coeffs[k];
     return AN5D_OK;
 }

@@ -12,6 +12,9 @@ namespace an5d {
 
 enum Dtype : int { DT_F32 = 0, DT_F64 = 1, DT_F16S = 2, DT_F32C = 3 };
 enum Shape : int { SH_STAR = 0, SH_BOX = 1 };
+// Per-step operation after the weighted sum (division-type stencils of Table 4):
+// none, an IEEE division by the divisor, or a product with its rounded reciprocal.
+enum Post : int { POST_NONE = 0, POST_DIV = 1, POST_MUL = 2 };
 
 constexpr int MAX_COEFFS = 729;  // (2R+1)^3 for the largest stencil, box3d radius 4
 
@@ -37,6 +40,7 @@ struct PassDesc {
     int total_units;         // warps (2D) or CTAs (3D) that carry work
     int ctas;                // grid size
     int stall_test;          // fault injection (tests only)
+    double post_c;           // divisor (POST_DIV) or reciprocal (POST_MUL), in the dtype's precision
     double coeffs[MAX_COEFFS];
 };
 
@@ -44,10 +48,11 @@ using LaunchFn = cudaError_t (*)(const PassDesc &, cudaStream_t);
 
 struct KernelKey {
     int ndim, shape, radius, dtype, bt;
+    int post = POST_NONE;
     bool operator==(const KernelKey &o) const
     {
         return ndim == o.ndim && shape == o.shape && radius == o.radius && dtype == o.dtype &&
-               bt == o.bt;
+               bt == o.bt && post == o.post;
     }
 };
 
@@ -82,6 +87,7 @@ namespace an5d {
 // Read-only view of a plan for translation units other than the C-ABI one.
 struct PlanView {
     int ndim, shape, radius, dtype, n, bt, hsn, device;
+    int post;              // POST_NONE unless the plan is a division-type stencil
     int64_t nz, ny, nx, total;
     size_t bytes;
     const double *coeffs;  // rounded to the compute precision

@@ -175,6 +175,18 @@ __device__ __forceinline__ float op_fma(float a, float b, float c) { return __fm
 __device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float op_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double op_add(double a, double b) { return __dadd_rn(a, b); }
+// IEEE division, round to nearest (CUDA's correctly rounded intrinsics).
+__device__ __forceinline__ float op_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double op_div(double a, double b) { return __ddiv_rn(a, b); }
+
+// Per-step operation of a division-type stencil on the finished weighted sum
+// x: none, x / c (POST_DIV) or x * c with c the rounded reciprocal (POST_MUL).
+template <int POST, typename C> __device__ __forceinline__ C post_op(C x, C c)
+{
+    if constexpr (POST == POST_DIV) return op_div(x, c);
+    else if constexpr (POST == POST_MUL) return op_mul(x, c);
+    else return x;
+}
 __device__ __forceinline__ float op_sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(a, b); }
 
@@ -252,6 +264,20 @@ __device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b)
     f2_t d;
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
+}
+
+// post_op on both halves of a packed pair; cp holds (c, c).
+template <int POST> __device__ __forceinline__ f2_t f2_post(f2_t x, f2_t cp, float c)
+{
+    if constexpr (POST == POST_MUL) {
+        return f2_mul(cp, x);
+    } else if constexpr (POST == POST_DIV) {
+        float lo, hi;
+        f2_unpack(x, lo, hi);
+        return f2_pack(op_div(lo, c), op_div(hi, c));
+    } else {
+        return x;
+    }
 }
 
 // Store predicated by bit `bit` of `mask`, without a branch.

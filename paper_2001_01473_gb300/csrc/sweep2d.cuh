@@ -54,6 +54,8 @@ template <typename S, int N> struct Sweep2DArgs {
     int stall_test;   // fault injection (tests only): warp 0's first row never completes
     CoeffBlock<typename StorageTraits<S>::C, N> k;
     CoeffBlock<unsigned long long, N> kp;  // FP32: (c_k, c_k) packed pairs for f32x2 arithmetic
+    typename StorageTraits<S>::C post_c;   // divisor or reciprocal (division-type stencils)
+    unsigned long long post_p;             // FP32: (post_c, post_c)
 };
 
 template <typename S, int BT, int R> struct Sweep2DGeom {
@@ -115,12 +117,17 @@ struct Tile2D {
 // With RAW the rows are fetched by non-tensor bulk copies from tg.src
 // (clamped to the array; the array's last partial 16-byte chunk by plain
 // loads) instead of through the tensor map: no descriptor to fetch, for
-// callers that switch arrays often.  Returns false if a bounded wait gave up.
+// callers that switch arrays often.  With POST (division-type stencils) every
+// level's weighted sum is divided by post_c, or multiplied by it when post_c
+// is the reciprocal (post_p: the pair (post_c, post_c)).  Returns false if a
+// bounded wait gave up.
 template <int SHAPE, int R, int BT, typename S, int MODE, bool PACK, typename CF, typename CP,
-          bool LEVELS = false, bool RAW = false>
+          bool LEVELS = false, bool RAW = false, int POST = POST_NONE>
 __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap *tmap, S *const dst,
                                              int *const status, unsigned char *const ring,
-                                             const CF &cf, const CP &cp, S *const *lvl = nullptr)
+                                             const CF &cf, const CP &cp, S *const *lvl = nullptr,
+                                             const typename StorageTraits<S>::C post_c = 0,
+                                             const f2_t post_p = 0)
 {
     using C = typename StorageTraits<S>::C;
     using G = Sweep2DGeom<S, BT, R>;
@@ -337,6 +344,10 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
                         for (int h = 0; h < H; ++h) acc[h] = f2_fma(cp[kk + 1], rr[t - 1][sy][h], acc[h]);
                         kk += 2;
                     }
+                    if constexpr (POST != POST_NONE) {
+#pragma unroll
+                        for (int h = 0; h < H; ++h) acc[h] = f2_post<POST>(acc[h], post_p, post_c);
+                    }
                     if (t < BT) {
                         if (EDGE) {
 #pragma unroll
@@ -453,9 +464,13 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
                     }
                     const int e_row = i - t * R;
                     const int se = ((k - t * R) % P + P) % P;
+                    // a halo row's pending value is its fixed copy: no per-step division
+                    const bool inner = !CHECK || (e_row >= R && e_row < ny + R);
                     float out_row[V];
 #pragma unroll
-                    for (int h = 0; h < H; ++h) f2_unpack(pa[t - 1][se][h], out_row[2 * h], out_row[2 * h + 1]);
+                    for (int h = 0; h < H; ++h)
+                        f2_unpack(inner ? f2_post<POST>(pa[t - 1][se][h], post_p, post_c) : pa[t - 1][se][h],
+                                  out_row[2 * h], out_row[2 * h + 1]);
                     if (t < BT) {
                         if (EDGE) {
                             int s2 = sb + (k - t * R);
@@ -543,7 +558,7 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
                     }
                     C res[V];
 #pragma unroll
-                    for (int v = 0; v < V; ++v) res[v] = level_round<S>(acc[v].result());
+                    for (int v = 0; v < V; ++v) res[v] = level_round<S>(post_op<POST>(acc[v].result(), post_c));
                     if (t < BT) {
                         if (EDGE) {
 #pragma unroll
@@ -631,8 +646,13 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
                     const int e = i - t * R;  // level-t row completed now
                     const int se = ((k - t * R) % P + P) % P;
                     C out_row[V];
+                    // a halo row's pending value is its fixed copy: no per-step division
+                    const bool inner = !CHECK || (e >= R && e < ny + R);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) out_row[v] = level_round<S>(pa[t - 1][se][v].result());
+                    for (int v = 0; v < V; ++v) {
+                        const C x = pa[t - 1][se][v].result();
+                        out_row[v] = level_round<S>(inner ? post_op<POST>(x, post_c) : x);
+                    }
                     if (t < BT) {
                         if (EDGE) {
                             // input value of row e, still in its ring slot k - t*R slots back
@@ -673,7 +693,7 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
     return true;
 }
 
-template <int SHAPE, int R, int BT, typename S, int MODE>
+template <int SHAPE, int R, int BT, typename S, int MODE, int POST>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE, BT, R, MODE>::value))
     sweep2d_kernel(const __grid_constant__ CUtensorMap tmap,
                    const Sweep2DArgs<S, NCoeff2<SHAPE, R>::value> a)
@@ -701,12 +721,13 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
     tg.stall = a.stall_test && gw == 0;
     unsigned char *const smem_al = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
-    sweep2d_tile<SHAPE, R, BT, S, MODE, true>(tg, &tmap, a.dst, a.status, smem_al + warp * G::WARP_BYTES,
-                                              a.k.c, a.kp.c);
+    sweep2d_tile<SHAPE, R, BT, S, MODE, true, decltype(a.k.c), decltype(a.kp.c), false, false, POST>(
+        tg, &tmap, a.dst, a.status, smem_al + warp * G::WARP_BYTES, a.k.c, a.kp.c, nullptr, a.post_c,
+        a.post_p);
 }
 
 // Host-side launcher of one instantiation.
-template <int SHAPE, int R, int BT, typename S, int MODE>
+template <int SHAPE, int R, int BT, typename S, int MODE, int POST>
 cudaError_t launch_sweep2d(const PassDesc &d, cudaStream_t st)
 {
     constexpr int N = NCoeff2<SHAPE, R>::value;
@@ -730,7 +751,14 @@ cudaError_t launch_sweep2d(const PassDesc &d, cudaStream_t st)
         memcpy(&u, &f, 4);
         a.kp.c[k] = ((unsigned long long)u << 32) | u;
     }
-    auto fn = sweep2d_kernel<SHAPE, R, BT, S, MODE>;
+    a.post_c = static_cast<C>(d.post_c);
+    {
+        const float f = static_cast<float>(d.post_c);
+        unsigned u;
+        memcpy(&u, &f, 4);
+        a.post_p = ((unsigned long long)u << 32) | u;
+    }
+    auto fn = sweep2d_kernel<SHAPE, R, BT, S, MODE, POST>;
     if (G::CTA_BYTES > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              G::CTA_BYTES);
@@ -740,14 +768,14 @@ cudaError_t launch_sweep2d(const PassDesc &d, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int SHAPE, int R, int BT, typename S, int MODE>
+template <int SHAPE, int R, int BT, typename S, int MODE, int POST = POST_NONE>
 KernelEntry entry2d(int dtype)
 {
     using G = Sweep2DGeom<S, BT, R>;
     KernelEntry e;
-    e.key = KernelKey{2, SHAPE, R, dtype, BT};
-    e.launch = &launch_sweep2d<SHAPE, R, BT, S, MODE>;
-    e.func = reinterpret_cast<const void *>(&sweep2d_kernel<SHAPE, R, BT, S, MODE>);
+    e.key = KernelKey{2, SHAPE, R, dtype, BT, POST};
+    e.launch = &launch_sweep2d<SHAPE, R, BT, S, MODE, POST>;
+    e.func = reinterpret_cast<const void *>(&sweep2d_kernel<SHAPE, R, BT, S, MODE, POST>);
     e.threads = WARPS_PER_CTA * 32;
     e.smem_bytes = G::CTA_BYTES;
     e.tile_x = G::TILE;

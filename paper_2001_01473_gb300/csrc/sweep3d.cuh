@@ -46,6 +46,7 @@ template <typename S, int N> struct Sweep3DArgs {
     int hsn;          // output planes per stream block
     int total_ctas;   // tiles_x * tiles_y * stream blocks
     CoeffBlock<typename StorageTraits<S>::C, N> k;
+    typename StorageTraits<S>::C post_c;  // divisor or reciprocal (division-type stencils)
 };
 
 template <typename S, int SHAPE, int BT, int R, int NW> struct Sweep3DGeom {
@@ -71,7 +72,7 @@ template <typename S, int SHAPE, int BT, int R, int NW> struct Sweep3DGeom {
     static_assert(TY <= 32, "one TMA row per lane of warp 0");
 };
 
-template <int SHAPE, int R, int BT, typename S, int MODE, int NW>
+template <int SHAPE, int R, int BT, typename S, int MODE, int NW, int POST>
 __global__ void __launch_bounds__(NW * 32, 1)
     sweep3d_kernel(const __grid_constant__ CUtensorMap tmap,
                    const Sweep3DArgs<S, NCoeff3<SHAPE, R>::value> a)
@@ -324,7 +325,8 @@ __global__ void __launch_bounds__(NW * 32, 1)
                             kk += 3;
                         }
 #pragma unroll
-                        for (int v = 0; v < V; ++v) res[r][v] = level_round<S>(acc[v].result());
+                        for (int v = 0; v < V; ++v)
+                            res[r][v] = level_round<S>(post_op<POST>(acc[v].result(), a.post_c));
                     }
                     if (t < BT) {
                         if (EDGE) {
@@ -426,11 +428,16 @@ __global__ void __launch_bounds__(NW * 32, 1)
                     }
                     const int e = i - t * R;  // level-t plane completed now
                     const int se = ((k - t * R) % P + P) % P;
+                    // a halo plane's pending value is its fixed copy: no per-step division
+                    const bool inner = !CHECK || (e >= R && e < nz + R);
                     C out[RW][V];
 #pragma unroll
                     for (int r = 0; r < RW; ++r)
 #pragma unroll
-                        for (int v = 0; v < V; ++v) out[r][v] = level_round<S>(pa[t - 1][se][r][v].result());
+                        for (int v = 0; v < V; ++v) {
+                            const C x = pa[t - 1][se][r][v].result();
+                            out[r][v] = level_round<S>(inner ? post_op<POST>(x, a.post_c) : x);
+                        }
                     if (t < BT) {
                         if (EDGE) {
                             int s = cs - t * R;  // plane e = i - t*R is t*R slots back
@@ -473,7 +480,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
     }
 }
 
-template <int SHAPE, int R, int BT, typename S, int MODE, int NW>
+template <int SHAPE, int R, int BT, typename S, int MODE, int NW, int POST>
 cudaError_t launch_sweep3d(const PassDesc &d, cudaStream_t st)
 {
     constexpr int N = NCoeff3<SHAPE, R>::value;
@@ -494,7 +501,8 @@ cudaError_t launch_sweep3d(const PassDesc &d, cudaStream_t st)
     a.hsn = d.hsn;
     a.total_ctas = d.total_units;
     for (int k = 0; k < N; ++k) a.k.c[k] = static_cast<C>(d.coeffs[k]);
-    auto fn = sweep3d_kernel<SHAPE, R, BT, S, MODE, NW>;
+    a.post_c = static_cast<C>(d.post_c);
+    auto fn = sweep3d_kernel<SHAPE, R, BT, S, MODE, NW, POST>;
     if (G::SMEM_BYTES > 48 * 1024) {
         cudaError_t e =
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
@@ -504,14 +512,14 @@ cudaError_t launch_sweep3d(const PassDesc &d, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int SHAPE, int R, int BT, typename S, int MODE, int NW>
+template <int SHAPE, int R, int BT, typename S, int MODE, int NW, int POST = POST_NONE>
 KernelEntry entry3d(int dtype)
 {
     using G = Sweep3DGeom<S, SHAPE, BT, R, NW>;
     KernelEntry e;
-    e.key = KernelKey{3, SHAPE, R, dtype, BT};
-    e.launch = &launch_sweep3d<SHAPE, R, BT, S, MODE, NW>;
-    e.func = reinterpret_cast<const void *>(&sweep3d_kernel<SHAPE, R, BT, S, MODE, NW>);
+    e.key = KernelKey{3, SHAPE, R, dtype, BT, POST};
+    e.launch = &launch_sweep3d<SHAPE, R, BT, S, MODE, NW, POST>;
+    e.func = reinterpret_cast<const void *>(&sweep3d_kernel<SHAPE, R, BT, S, MODE, NW, POST>);
     e.threads = NW * 32;
     e.smem_bytes = G::SMEM_BYTES;
     e.tile_x = G::TX;

@@ -237,6 +237,7 @@ cudaError_t launch_box1(const PassDesc &d, cudaStream_t st)
     a.hsn = d.hsn;
     a.total_ctas = d.total_units;
     for (int k = 0; k < N; ++k) a.k.c[k] = static_cast<C>(d.coeffs[k]);
+    a.post_c = C(0);
     auto fn = box1_kernel<R, S, NW, RW_>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
     if (e != cudaSuccess) return e;

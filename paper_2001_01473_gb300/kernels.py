@@ -74,6 +74,26 @@ KERNELS_3D_BOX1 = [
 ]
 
 
+# Division-type stencils (Table 4: j2d5pt = star2d R1, j2d9pt = star2d R2,
+# j2d9pt-gol = box2d R1, j3d27pt = box3d R1, each divided by a constant every
+# step), in both forms of the division: (shape, radius, bT range, storage
+# type, dtype tag) and, in 3D, warps per CTA.
+POSTS = ("POST_DIV", "POST_MUL")
+KERNELS_DIV_2D = [
+    (STAR, 1, range(1, 11), "float", "DT_F32"),
+    (STAR, 2, range(1, 6), "float", "DT_F32"),
+    (BOX, 1, range(1, 7), "float", "DT_F32"),
+    (STAR, 1, range(1, 3), "double", "DT_F64"),
+    (STAR, 2, range(1, 3), "double", "DT_F64"),
+    (BOX, 1, range(1, 3), "double", "DT_F64"),
+]
+KERNELS_DIV_3D = [
+    (BOX, 1, range(1, 3), "float", "DT_F32", 16),
+    (BOX, 1, range(3, 4), "float", "DT_F32", 12),
+    (BOX, 1, range(1, 2), "double", "DT_F64", 12),
+]
+
+
 def instantiations():
     """Yield (header, entry expression) for every kernel instantiation."""
     for shape, r, bts, s, mode, dt in KERNELS_2D:
@@ -84,3 +104,10 @@ def instantiations():
             yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, {mode}, {nw}>({dt})"
     for r, s, dt, nw, rw in KERNELS_3D_BOX1:
         yield "sweep3d_box1.cuh", f"entry_box1<{r}, {s}, {nw}, {rw}>({dt})"
+    for post in POSTS:
+        for shape, r, bts, s, dt in KERNELS_DIV_2D:
+            for bt in bts:
+                yield "sweep2d.cuh", f"entry2d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {post}>({dt})"
+        for shape, r, bts, s, dt, nw in KERNELS_DIV_3D:
+            for bt in bts:
+                yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {nw}, {post}>({dt})"

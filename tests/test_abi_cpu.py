@@ -91,3 +91,17 @@ def test_plan_create_without_device_reports_cuda_error(lib):
     with pytest.raises(an5d.An5dError) as e:
         an5d.an5d_plan_create(2, inputs.STAR, 1, np.ones(5), "f32", [16, 16])
     assert e.value.status in (an5d.AN5D_ERR_CUDA, an5d.AN5D_ERR_OOM)
+
+
+def test_plan_create_div_rejects_bad_arguments(lib):
+    c = np.ones(5)
+    for kw, status in ((dict(divisor=7.0, post=3, dtype="f32"), an5d.AN5D_ERR_INVALID_ARG),
+                       (dict(divisor=0.0, post="div", dtype="f32"), an5d.AN5D_ERR_INVALID_ARG),
+                       (dict(divisor=float("inf"), post="rcp", dtype="f64"), an5d.AN5D_ERR_INVALID_ARG),
+                       (dict(divisor=1e-300, post="div", dtype="f32"), an5d.AN5D_ERR_INVALID_ARG),
+                       (dict(divisor=7.0, post="div", dtype="f16"), an5d.AN5D_ERR_UNSUPPORTED),
+                       (dict(divisor=7.0, post="div", dtype="f32c"), an5d.AN5D_ERR_UNSUPPORTED)):
+        with pytest.raises(an5d.An5dError) as e:
+            an5d.an5d_plan_create_div(2, inputs.STAR, 1, c, kw["divisor"], kw["post"], kw["dtype"],
+                                      [8, 8])
+        assert e.value.status == status, kw
