@@ -272,6 +272,53 @@ def committed_traffic(workload: str, bt: int):
 
 
 # ---------------------------------------------------------------------------
+# The paper's analytic model (Section 4) next to the measurement.
+
+PAPER_FP64_NOMINAL_GFLOPS = 1250.0   # GB300's nominal FP64 rate (the model takes theoretical compute)
+
+
+def paper_model_report(an5d, ndim, shape, R, dtype, dims, post, bt, hsn, tile, value, inrun):
+    """The paper's model on this GPU's peaks (compute: nominal FMA rate from the
+    unit counts; global and shared memory: the in-run micro-benchmarks), for
+    (a) this run's configuration read as the paper's design (one thread per
+    cell of the tile) and (b) the model's own best configuration over the
+    paper's tuning space (Section 5.3).  accuracy = measured / predicted, the
+    paper's model-accuracy ratio (Section 6.3)."""
+    if dtype not in ("f32", "f64"):
+        return None
+    n = inputs.coeff_count(ndim, shape, R)
+    ops = (n - 1, 1, 0, 1 if post else 0)
+    comp = (PAPER_FP64_NOMINAL_GFLOPS if dtype == "f64"
+            else inrun["sms"] * 128 * 2 * inrun["sm_clock_mhz"] * 1e-3)
+    dev = dict(peak_comp_gflops=comp, peak_gm_gbs=inrun["hbm_gbs"], peak_sm_gbs=inrun["smem_gbs"],
+               sm_count=inrun["sms"], max_threads_per_sm=2048)
+    w = bytes_per_cell(dtype)
+    out = {"peaks": dev}
+    try:
+        r = an5d.an5d_paper_model(ndim, shape, R, w, ops, dims, bt, tile, hsn, dev)
+        out["at_this_config"] = {"bT": bt, "bS": tile, "hSN": hsn, "gcells": r["gcells"],
+                                 "bound": r["bound"], "accuracy": value / r["gcells"]}
+    except an5d.An5dError:
+        pass
+    best = None
+    bts = range(1, 17) if ndim == 2 else range(1, 9)
+    bss = [[128], [256], [512], [1024]] if ndim == 2 else [[16, 16], [32, 16], [32, 32], [64, 16]]
+    for b in bts:
+        for bs in bss:
+            for h in (128, 256, 512, 1024):
+                try:
+                    r = an5d.an5d_paper_model(ndim, shape, R, w, ops, dims, b, bs, h, dev)
+                except an5d.An5dError:
+                    continue
+                if best is None or r["gcells"] > best["gcells"]:
+                    best = {"bT": b, "bS": bs, "hSN": h, "gcells": r["gcells"], "bound": r["bound"]}
+    if best:
+        best["accuracy"] = value / best["gcells"]
+        out["model_best"] = best
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Reference arm: the CPU oracle.
 
 def oracle_time(ndim, shape, R, dtype, dims, budget_s=12.0, post=None):
@@ -476,6 +523,9 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
         "inrun_peaks": inrun,
+        "paper_model": paper_model_report(an5d, ndim, shape, R, dtype, dims, post, bt, cfg["hsn"],
+                                          [cfg["tile_x"]] + ([cfg["tile_y"]] if ndim == 3 else []),
+                                          value, inrun),
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -335,6 +335,54 @@ typedef struct {
  * Synchronous; allocates and frees 2 GiB of device memory. */
 int an5d_measure_peaks(an5d_peaks *out, void *stream);
 
+/* The paper's analytic performance model (Section 4), evaluated on the host
+ * for the paper's own kernel design: one thread per cell of a spatial block
+ * bS[0] x ... (x first), threads classed as out-of-bound, boundary, redundant
+ * or valid; global-memory traffic one read per in-grid thread at level 0 and
+ * one write per valid thread at level bT; shared-memory traffic one write per
+ * thread and level below bT plus Table 3's practical reads per computing or
+ * boundary thread; compute over the region of valid computation of each
+ * level (bS - 2tR per axis); time = max(compute / (peak x eff_ALU), global /
+ * peak, shared / peak) / eff_SM.  It is independent of this library's
+ * kernels (whose own model ranks the tuner's candidates) and needs no GPU.
+ *   st     stencil: ndim, shape, radius, word bytes, and its operations per
+ *          cell-update as FMA / MUL / ADD / other (star and box: n-1 FMA and
+ *          one MUL; eff_ALU = (2 FMA + MUL + ADD + other) / (2 x all))
+ *   dims   ndim interior extents, slowest (streamed) first
+ *   bT     temporal degree (>= 1); bS: ndim-1 block sizes, x first, each
+ *          greater than 2 bT R; hSN: planes per stream block (>= 1)
+ *   dev    peaks: compute (GFLOP/s of the dtype), global and shared memory
+ *          throughput (GB/s), SM count, resident threads per SM
+ *   out    thread counts and totals of one pass (bT steps) over the grid,
+ *          the three times and the model time (seconds), and the predicted
+ *          useful rate (GCell-updates/s and GFLOP/s at the stencil's flops)
+ * Returns AN5D_OK or AN5D_ERR_INVALID_ARG. */
+typedef struct {
+    int ndim;
+    an5d_shape shape;
+    int radius;
+    int word_bytes;
+    int op_fma, op_mul, op_add, op_other;
+} an5d_paper_stencil;
+typedef struct {
+    double peak_comp_gflops;
+    double peak_gm_gbs;
+    double peak_sm_gbs;
+    int sm_count;
+    int max_threads_per_sm;
+} an5d_paper_device;
+typedef struct {
+    double th_comp, th_sm_read, th_sm_write, th_gm_read, th_gm_write;
+    double total_comp, total_gm, total_sm;  /* flop, bytes, bytes per pass */
+    double eff_alu, eff_sm;
+    double time_comp, time_gm, time_sm, time_model;
+    double gcells, gflops;
+    int64_t n_tb;                           /* thread blocks per pass */
+    int bound;                              /* 0 compute, 1 global memory, 2 shared memory */
+} an5d_paper_model_result;
+int an5d_paper_model(const an5d_paper_stencil *st, const int64_t *dims, int bT, const int *bS,
+                     int hSN, const an5d_paper_device *dev, an5d_paper_model_result *out);
+
 /* Current peaks of the current device: measured if an5d_measure_peaks ran
  * in this process, else nominal figures from the device attributes. */
 int an5d_get_peaks(an5d_peaks *out);

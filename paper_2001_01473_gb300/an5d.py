@@ -37,6 +37,26 @@ class An5dError(RuntimeError):
         self.status = status
 
 
+class an5d_paper_stencil(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("shape", ctypes.c_int), ("radius", ctypes.c_int),
+                ("word_bytes", ctypes.c_int), ("op_fma", ctypes.c_int), ("op_mul", ctypes.c_int),
+                ("op_add", ctypes.c_int), ("op_other", ctypes.c_int)]
+
+
+class an5d_paper_device(ctypes.Structure):
+    _fields_ = [("peak_comp_gflops", ctypes.c_double), ("peak_gm_gbs", ctypes.c_double),
+                ("peak_sm_gbs", ctypes.c_double), ("sm_count", ctypes.c_int),
+                ("max_threads_per_sm", ctypes.c_int)]
+
+
+class an5d_paper_model_result(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "th_comp", "th_sm_read", "th_sm_write", "th_gm_read", "th_gm_write",
+        "total_comp", "total_gm", "total_sm", "eff_alu", "eff_sm",
+        "time_comp", "time_gm", "time_sm", "time_model", "gcells", "gflops")] + [
+        ("n_tb", ctypes.c_int64), ("bound", ctypes.c_int)]
+
+
 class an5d_config(ctypes.Structure):
     _fields_ = [("bT", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("stream_axis", ctypes.c_int), ("hsn", ctypes.c_int),
@@ -89,6 +109,10 @@ def load(path: str = LIB_PATH):
     L.an5d_plan_create.restype = P
     L.an5d_plan_create_div.argtypes = [I, I, I, P, ctypes.c_double, I, I, P]
     L.an5d_plan_create_div.restype = P
+    L.an5d_paper_model.argtypes = [ctypes.POINTER(an5d_paper_stencil), P, I, P, I,
+                                   ctypes.POINTER(an5d_paper_device),
+                                   ctypes.POINTER(an5d_paper_model_result)]
+    L.an5d_paper_model.restype = I
     L.an5d_run.argtypes = [P, P, P, I64, P]
     L.an5d_run.restype = I
     L.an5d_run_host.argtypes = [P, P, P, I64, P]
@@ -281,6 +305,25 @@ def an5d_get_peaks() -> dict:
     pk = an5d_peaks()
     _check(load().an5d_get_peaks(ctypes.byref(pk)))
     return pk.as_dict()
+
+
+def an5d_paper_model(ndim: int, shape: int, radius: int, word_bytes: int, ops, dims, bT: int,
+                     bS, hSN: int, device: dict) -> dict:
+    """The paper's analytic model (see an5d.h).  ops = (fma, mul, add, other)
+    per cell-update; bS: block sizes, x first; device: peak_comp_gflops,
+    peak_gm_gbs, peak_sm_gbs, sm_count, max_threads_per_sm."""
+    st = an5d_paper_stencil(ndim, shape, radius, word_bytes, *[int(v) for v in ops])
+    dv = an5d_paper_device(float(device["peak_comp_gflops"]), float(device["peak_gm_gbs"]),
+                           float(device["peak_sm_gbs"]), int(device["sm_count"]),
+                           int(device.get("max_threads_per_sm", 2048)))
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int64))
+    b = np.ascontiguousarray(np.asarray(bS, dtype=np.int32))
+    out = an5d_paper_model_result()
+    _check(load().an5d_paper_model(ctypes.byref(st), d.ctypes.data, int(bT), b.ctypes.data,
+                                   int(hSN), ctypes.byref(dv), ctypes.byref(out)))
+    r = {n: getattr(out, n) for n, _ in an5d_paper_model_result._fields_}
+    r["bound"] = ("compute", "global", "shared")[out.bound]
+    return r
 
 
 POST_DIV, POST_MUL_RCP = 1, 2
