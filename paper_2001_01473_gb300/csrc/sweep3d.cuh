@@ -7,8 +7,9 @@
 // of hsn planes (Section 3.2, division of the streaming dimension).
 //
 // GB300 mapping (this library's design):
-//  * a CTA of NW warps owns a tile of TY = 2*NW rows (y) by 128 cells (x);
-//    each warp owns two rows, each lane 4 consecutive x cells of both rows;
+//  * a CTA of NW warps owns a tile of TY = RW*NW rows (y) by TX = 32*V cells
+//    (x); each warp owns RW rows, each lane V consecutive x cells of them
+//    (V = 4, RW = 2 by default; V = 2, RW = 4 gives 64-cell-wide tiles);
 //  * input planes are staged by TMA, one 1D row copy per lane of warp 0,
 //    into a shared-memory ring of planes guarded by one mbarrier per plane;
 //  * each level keeps the 2R+1 most recent planes of the thread's 8 cells
@@ -49,9 +50,10 @@ template <typename S, int N> struct Sweep3DArgs {
     typename StorageTraits<S>::C post_c;  // divisor or reciprocal (division-type stencils)
 };
 
-template <typename S, int SHAPE, int BT, int R, int NW> struct Sweep3DGeom {
-    static constexpr int V = CELLS_PER_LANE;
-    static constexpr int RW = 2;                 // rows per warp
+template <typename S, int SHAPE, int BT, int R, int NW, int V_ = CELLS_PER_LANE, int RW_ = 2>
+struct Sweep3DGeom {
+    static constexpr int V = V_;                 // consecutive x cells per lane
+    static constexpr int RW = RW_;               // rows per warp
     static constexpr int TY = NW * RW;           // tile rows
     static constexpr int TX = 32 * V;            // tile columns
     static constexpr int P = 2 * R + 1;
@@ -69,16 +71,16 @@ template <typename S, int SHAPE, int BT, int R, int NW> struct Sweep3DGeom {
     static_assert(SMEM_BYTES <= 232448, "shared memory per CTA exceeds 227 KB");
     static_assert(TX - 2 * BT * R >= 8 && TY - 2 * BT * R >= 2, "tile too small for bT*R");
     static_assert(R <= V, "radius must not exceed cells per lane");
-    static_assert(TY <= 32, "one TMA row per lane of warp 0");
+    static_assert(RW * V <= 32, "cell bit masks");
 };
 
-template <int SHAPE, int R, int BT, typename S, int MODE, int NW, int POST>
+template <int SHAPE, int R, int BT, typename S, int MODE, int NW, int POST, int V_, int RW_>
 __global__ void __launch_bounds__(NW * 32, 1)
     sweep3d_kernel(const __grid_constant__ CUtensorMap tmap,
                    const Sweep3DArgs<S, NCoeff3<SHAPE, R>::value> a)
 {
     using C = typename StorageTraits<S>::C;
-    using G = Sweep3DGeom<S, SHAPE, BT, R, NW>;
+    using G = Sweep3DGeom<S, SHAPE, BT, R, NW, V_, RW_>;
     constexpr int V = G::V, RW = G::RW, TY = G::TY, TX = G::TX, P = G::P, D = G::D, A = G::A,
                   PF = G::PF;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -125,14 +127,15 @@ __global__ void __launch_bounds__(NW * 32, 1)
     uint64_t *const bars = reinterpret_cast<uint64_t *>(base + D * G::SLOT_BYTES + G::XB_BYTES);
     int *const status = a.status;
 
-    // TMA of the tile rows of plane p into ring slot s: lane r of warp 0 copies row r.
+    // TMA of the tile rows of plane p into ring slot s: lane r of warp 0
+    // copies rows r, r + 32, ...
     auto issue_plane = [&](int p, int s) {
         if (lane == 0) mbar_expect_tx(&bars[s], TY * G::ROWBUF * (int)sizeof(S));
         __syncwarp();
-        if (lane < TY) {
-            const int lin = (p * py + yb + lane) * px + x0;
+        for (int r = lane; r < TY; r += 32) {
+            const int lin = (p * py + yb + r) * px + x0;
             fence_proxy_async();
-            tma_load_1d(ring + s * G::SLOT_BYTES + lane * G::ROW_BYTES, &tmap, lin & ~(A - 1), &bars[s]);
+            tma_load_1d(ring + s * G::SLOT_BYTES + r * G::ROW_BYTES, &tmap, lin & ~(A - 1), &bars[s]);
         }
     };
     // This thread's cells of tile row (warp*RW + r) of plane p in slot s.
@@ -480,12 +483,12 @@ __global__ void __launch_bounds__(NW * 32, 1)
     }
 }
 
-template <int SHAPE, int R, int BT, typename S, int MODE, int NW, int POST>
+template <int SHAPE, int R, int BT, typename S, int MODE, int NW, int POST, int V_, int RW_>
 cudaError_t launch_sweep3d(const PassDesc &d, cudaStream_t st)
 {
     constexpr int N = NCoeff3<SHAPE, R>::value;
     using C = typename StorageTraits<S>::C;
-    using G = Sweep3DGeom<S, SHAPE, BT, R, NW>;
+    using G = Sweep3DGeom<S, SHAPE, BT, R, NW, V_, RW_>;
     Sweep3DArgs<S, N> a;
     a.dst = static_cast<S *>(d.dst);
     a.status = d.status;
@@ -502,7 +505,7 @@ cudaError_t launch_sweep3d(const PassDesc &d, cudaStream_t st)
     a.total_ctas = d.total_units;
     for (int k = 0; k < N; ++k) a.k.c[k] = static_cast<C>(d.coeffs[k]);
     a.post_c = static_cast<C>(d.post_c);
-    auto fn = sweep3d_kernel<SHAPE, R, BT, S, MODE, NW, POST>;
+    auto fn = sweep3d_kernel<SHAPE, R, BT, S, MODE, NW, POST, V_, RW_>;
     if (G::SMEM_BYTES > 48 * 1024) {
         cudaError_t e =
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
@@ -512,14 +515,15 @@ cudaError_t launch_sweep3d(const PassDesc &d, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int SHAPE, int R, int BT, typename S, int MODE, int NW, int POST = POST_NONE>
+template <int SHAPE, int R, int BT, typename S, int MODE, int NW, int POST = POST_NONE,
+          int V_ = CELLS_PER_LANE, int RW_ = 2>
 KernelEntry entry3d(int dtype)
 {
-    using G = Sweep3DGeom<S, SHAPE, BT, R, NW>;
+    using G = Sweep3DGeom<S, SHAPE, BT, R, NW, V_, RW_>;
     KernelEntry e;
     e.key = KernelKey{3, SHAPE, R, dtype, BT, POST};
-    e.launch = &launch_sweep3d<SHAPE, R, BT, S, MODE, NW, POST>;
-    e.func = reinterpret_cast<const void *>(&sweep3d_kernel<SHAPE, R, BT, S, MODE, NW, POST>);
+    e.launch = &launch_sweep3d<SHAPE, R, BT, S, MODE, NW, POST, V_, RW_>;
+    e.func = reinterpret_cast<const void *>(&sweep3d_kernel<SHAPE, R, BT, S, MODE, NW, POST, V_, RW_>);
     e.threads = NW * 32;
     e.smem_bytes = G::SMEM_BYTES;
     e.tile_x = G::TX;

@@ -62,6 +62,15 @@ KERNELS_3D = [
 ]
 
 
+# 3D tile shape per stencil: (cells per lane V, rows per warp RW); the CTA
+# tile is (NW * RW) rows x (32 * V) cells.  128 x 2 by default; the FP64
+# radius-1 star uses 64-cell-wide tiles of 4 rows per warp, which waste
+# fewer overlap cells on 512-wide grids (measured faster there; in FP32 the
+# extra shuffles and row addressing cost more than the overlap saves).
+def geom3d(shape, r, s):
+    return (2, 4) if (s == "double" and shape == STAR and r == 1) else (4, 2)
+
+
 # One-level 3D box sweeps for radius 2-4 (sweep3d_box1.cuh): (radius, storage
 # type, dtype tag, warps per CTA, rows per warp).  Each runs at bT = 1.
 KERNELS_3D_BOX1 = [
@@ -100,8 +109,9 @@ def instantiations():
         for bt in bts:
             yield "sweep2d.cuh", f"entry2d<{shape}, {r}, {bt}, {s}, {mode}>({dt})"
     for shape, r, bts, s, mode, dt, nw in KERNELS_3D:
+        v, rw = geom3d(shape, r, s)
         for bt in bts:
-            yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, {mode}, {nw}>({dt})"
+            yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, {mode}, {nw}, POST_NONE, {v}, {rw}>({dt})"
     for r, s, dt, nw, rw in KERNELS_3D_BOX1:
         yield "sweep3d_box1.cuh", f"entry_box1<{r}, {s}, {nw}, {rw}>({dt})"
     for post in POSTS:
@@ -109,5 +119,6 @@ def instantiations():
             for bt in bts:
                 yield "sweep2d.cuh", f"entry2d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {post}>({dt})"
         for shape, r, bts, s, dt, nw in KERNELS_DIV_3D:
+            v, rw = geom3d(shape, r, s)
             for bt in bts:
-                yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {nw}, {post}>({dt})"
+                yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {nw}, {post}, {v}, {rw}>({dt})"
