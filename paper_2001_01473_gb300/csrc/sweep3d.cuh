@@ -10,8 +10,10 @@
 //  * a CTA of NW warps owns a tile of TY = RW*NW rows (y) by TX = 32*V cells
 //    (x); each warp owns RW rows, each lane V consecutive x cells of them
 //    (V = 4, RW = 2 by default; V = 2, RW = 4 gives 64-cell-wide tiles);
-//  * input planes are staged by TMA, one 1D row copy per lane of warp 0,
-//    into a shared-memory ring of planes guarded by one mbarrier per plane;
+//  * input planes are staged by TMA into a shared-memory ring of planes:
+//    each warp copies its own rows (one 1D row copy per lane) and waits on
+//    its own mbarrier per ring slot, so no warp serialises a whole plane's
+//    copies and the ring needs no CTA-wide synchronisation;
 //  * each level keeps the 2R+1 most recent planes of the thread's 8 cells
 //    (star) or 2R+1 pending per-plane partial sums (box) in registers, in a
 //    fixed ring indexed by plane mod (2R+1) (Section 3.2 register allocation);
@@ -67,7 +69,7 @@ struct Sweep3DGeom {
     static constexpr int D = PF + KEEP + 1;                        // ring depth (planes)
     using C = typename StorageTraits<S>::C;
     static constexpr int XB_BYTES = 2 * TY * TX * (int)sizeof(C);  // y-exchange, double buffered
-    static constexpr int SMEM_BYTES = D * SLOT_BYTES + XB_BYTES + D * 8 + 128;
+    static constexpr int SMEM_BYTES = D * SLOT_BYTES + XB_BYTES + D * NW * 8 + 128;
     static_assert(SMEM_BYTES <= 232448, "shared memory per CTA exceeds 227 KB");
     static_assert(TX - 2 * BT * R >= 8 && TY - 2 * BT * R >= 2, "tile too small for bT*R");
     static_assert(R <= V, "radius must not exceed cells per lane");
@@ -127,16 +129,22 @@ __global__ void __launch_bounds__(NW * 32, 1)
     uint64_t *const bars = reinterpret_cast<uint64_t *>(base + D * G::SLOT_BYTES + G::XB_BYTES);
     int *const status = a.status;
 
-    // TMA of the tile rows of plane p into ring slot s: lane r of warp 0
-    // copies rows r, r + 32, ...
+    // Every warp stages its own RW rows of each plane (lane r copies row
+    // warp*RW + r) and waits on its own mbarrier per slot: a warp reads only
+    // its own staged rows, so the ring needs no CTA-wide synchronisation, and
+    // no single warp serialises the plane's row copies.
+    int nissue = ib0;  // next plane this warp requests
     auto issue_plane = [&](int p, int s) {
-        if (lane == 0) mbar_expect_tx(&bars[s], TY * G::ROWBUF * (int)sizeof(S));
+        if (lane == 0) mbar_expect_tx(&bars[s * NW + warp], RW * G::ROWBUF * (int)sizeof(S));
         __syncwarp();
-        for (int r = lane; r < TY; r += 32) {
-            const int lin = (p * py + yb + r) * px + x0;
+        if (lane < RW) {
+            const int row = warp * RW + lane;
+            const int lin = (p * py + yb + row) * px + x0;
             fence_proxy_async();
-            tma_load_1d(ring + s * G::SLOT_BYTES + r * G::ROW_BYTES, &tmap, lin & ~(A - 1), &bars[s]);
+            tma_load_1d(ring + s * G::SLOT_BYTES + row * G::ROW_BYTES, &tmap, lin & ~(A - 1),
+                        &bars[s * NW + warp]);
         }
+        nissue = p + 1;
     };
     // This thread's cells of tile row (warp*RW + r) of plane p in slot s.
     auto cells_in_slot = [&](int p, int s, int r) -> const S * {
@@ -146,16 +154,15 @@ __global__ void __launch_bounds__(NW * 32, 1)
     };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < D * NW; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (warp == 0)
-        for (int q = 0; q < PF; ++q)
-            if (ib0 + q < pend) issue_plane(ib0 + q, q);
+    for (int q = 0; q < PF; ++q)
+        if (ib0 + q < pend) issue_plane(ib0 + q, q);
 
-    // Ring position of the current plane i: slot cs, mbarrier phase cpar.
-    int cs = 0;
+    // Ring position of plane cur_p: slot cs, mbarrier phase cpar.
+    int cs = 0, cur_p = ib0;
     uint32_t cpar = 0;
     int xsel = 0;        // exchange buffer in use
     // First plane whose wait gave up, with its slot and phase (-1: none).
@@ -166,19 +173,19 @@ __global__ void __launch_bounds__(NW * 32, 1)
     S *const dst = a.dst;
 
     // Start of iteration i: request plane i+PF (its slot last held plane
-    // i+PF-D, consumed before the previous iteration's barriers), then wait
-    // for plane i and copy this thread's cells to registers.  After a wait
-    // gives up the warp stops requesting planes and keeps computing on zeros,
-    // so that every CTA barrier of the group is still reached; the pass's
+    // i+PF-D, whose rows of this warp it has read already), then wait for
+    // plane i and copy this thread's cells to registers.  After a wait gives
+    // up the warp stops requesting planes and keeps computing on zeros, so
+    // that every CTA barrier of the group is still reached; the pass's
     // result is then discarded (the plan's status reports the timeout).
     auto load_plane = [&](int i, bool have, C (&cell)[RW][V], bool &ok) {
-        if (warp == 0 && ok && i + PF < pend) {
+        if (ok && i + PF < pend) {
             int s = cs + PF;
             if (s >= D) s -= D;
             issue_plane(i + PF, s);
         }
         if (have && ok) {
-            ok = mbar_wait_warp(&bars[cs], cpar, status);
+            ok = mbar_wait_warp(&bars[cs * NW + warp], cpar, status);
             if (!ok) {
                 fpl = i;
                 fcs = cs;
@@ -200,19 +207,22 @@ __global__ void __launch_bounds__(NW * 32, 1)
         }
     };
     auto advance = [&]() {
+        ++cur_p;
         if (++cs == D) {
             cs = 0;
             cpar ^= 1u;
         }
     };
-    // After a timeout: the warp that gave up waits (bounded) for the copies
-    // still in flight, planes fpl .. fpl+PF, so none lands after exit.
+    // After a timeout anywhere in the CTA every warp leaves; first it waits
+    // (bounded) for its own copies still in flight, from the first plane it
+    // has not consumed (or the one whose wait gave up) to the last it
+    // requested, so that none lands after the CTA exits.
     auto drain = [&](int) {
-        if (fpl < 0) return;
-        int s = fcs;
-        uint32_t ph = fpar;
-        for (int p = fpl; p <= fpl + PF && p < pend; ++p) {
-            if (!mbar_wait_warp(&bars[s], ph, status)) break;
+        int p0 = cur_p, s = cs;
+        uint32_t ph = cpar;
+        if (fpl >= 0) p0 = fpl, s = fcs, ph = fpar;
+        for (int p = p0; p < nissue; ++p) {
+            if (!mbar_wait_warp(&bars[s * NW + warp], ph, status)) break;
             if (++s == D) {
                 s = 0;
                 ph ^= 1u;

@@ -10,8 +10,9 @@
 // GB300 mapping (this library's design):
 //  * a CTA of NW warps owns a tile of TY = RW*NW rows (y) by 128 cells (x),
 //    streams z, and stores the (TY-2R) x (128-2R) interior of its tile;
-//  * input planes are staged by TMA (one 1D row copy per lane of warp 0)
-//    into a shared-memory ring of planes guarded by one mbarrier per plane;
+//  * input planes are staged by TMA (every warp copies its own rows, one
+//    1D row copy per lane) into a shared-memory ring of planes guarded by one
+//    mbarrier per plane that all warps arrive on;
 //    every thread reads its neighbours in y and x straight from the staged
 //    plane (no shuffles, no exchange buffer);
 //  * the 2R+1 output planes in flight are partial sums in registers
@@ -40,7 +41,9 @@ template <typename S, int R, int NW, int RW_> struct Box1Geom {
     static constexpr int ROW_BYTES = ((ROWBUF * (int)sizeof(S) + 127) / 128) * 128;
     static constexpr int SLOT_BYTES = TY * ROW_BYTES;
     static constexpr int PF = PREFETCH_ROWS;     // planes in flight ahead
-    static constexpr int D = PF + 1;             // ring depth (planes)
+    // ring depth: the slot refilled at plane p held plane p - 2, which every
+    // warp finished reading before the previous plane's CTA barrier
+    static constexpr int D = PF + 2;
     // Lane 0 reads up to R cells left of its row's staged data: the ring
     // starts PAD bytes into the allocation so those reads stay inside it.
     // On the right, lane 31 reads up to A-1+R cells past the 128-cell tile,
@@ -51,7 +54,7 @@ template <typename S, int R, int NW, int RW_> struct Box1Geom {
     static_assert(R * (int)sizeof(S) <= PAD, "left reads must stay in the pad");
     static_assert((A - 1 + TX + R) * (int)sizeof(S) <= ROW_BYTES, "right reads must stay in the row");
     static_assert(TX - 2 * R >= 8 && TY - 2 * R >= 2, "tile too small for R");
-    static_assert(TY <= 32, "one TMA row per lane of warp 0");
+    static_assert(RW <= 32, "one TMA row per lane");
 };
 
 template <int R, typename S, int NW, int RW_>
@@ -101,26 +104,29 @@ __global__ void __launch_bounds__(NW * 32, 1)
     uint64_t *const bars = reinterpret_cast<uint64_t *>(ring + D * G::SLOT_BYTES);
     int *const status = a.status;
 
-    // TMA of the tile rows of plane p into ring slot s: lane r of warp 0 copies row r.
+    // TMA of the tile rows of plane p into ring slot s: every warp copies its
+    // own RW rows (lane r copies row warp*RW + r) and arrives on the slot's
+    // mbarrier with their byte count; the plane is complete when all NW
+    // warps arrived and every row landed.
     auto issue_plane = [&](int p, int s) {
-        if (lane == 0) mbar_expect_tx(&bars[s], TY * G::ROWBUF * (int)sizeof(S));
+        if (lane == 0) mbar_expect_tx(&bars[s], RW * G::ROWBUF * (int)sizeof(S));
         __syncwarp();
-        if (lane < TY) {
-            const long lin = (long)p * plane + (long)(yb + lane) * px + x0;
+        if (lane < RW) {
+            const int row = warp * RW + lane;
+            const long lin = (long)p * plane + (long)(yb + row) * px + x0;
             fence_proxy_async();
-            tma_load_1d(ring + s * G::SLOT_BYTES + lane * G::ROW_BYTES, &tmap,
+            tma_load_1d(ring + s * G::SLOT_BYTES + row * G::ROW_BYTES, &tmap,
                         (int)(lin & ~long(A - 1)), &bars[s]);
         }
     };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < D; ++s) mbar_init(&bars[s], NW);
         fence_mbar_init();
     }
     __syncthreads();
-    if (warp == 0)
-        for (int q = 0; q < PF; ++q)
-            if (pbeg + q < pend) issue_plane(pbeg + q, q);
+    for (int q = 0; q < PF; ++q)
+        if (pbeg + q < pend) issue_plane(pbeg + q, q);
 
     // acc[d][r][v]: pending output plane p - R + d (it next receives the
     // dz = R - d block of plane p); acc[0] completes with plane p.
@@ -137,14 +143,15 @@ __global__ void __launch_bounds__(NW * 32, 1)
     int cs = 0;
     uint32_t cpar = 0;
     for (int p = pbeg; p < pend; ++p) {
-        if (warp == 0 && p + PF < pend) {
+        if (p + PF < pend) {
             int s = cs + PF;
             if (s >= D) s -= D;
             issue_plane(p + PF, s);
         }
         const bool ok = mbar_wait_warp(&bars[cs], cpar, status);
         if (!__syncthreads_and(ok)) {
-            // the warps that gave up wait (bounded) for their copies still in flight
+            // the warps that gave up wait (bounded) for the copies still in flight
+            // (every warp's rows of planes p .. p+PF land on these mbarriers)
             if (!ok) {
                 int s = cs;
                 uint32_t ph = cpar;
