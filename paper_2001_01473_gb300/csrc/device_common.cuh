@@ -147,6 +147,57 @@ __device__ __forceinline__ typename StorageTraits<S>::C load_c(S v)
 }
 template <> __device__ __forceinline__ float load_c<__half>(__half v) { return __half2float(v); }
 
+// V consecutive storage elements at p, converted to the compute type, read
+// with the widest access the address's alignment allows.  A row staged by
+// TMA keeps the global array's misalignment, so p's alignment is the same
+// for every lane of a warp and the branch does not diverge; an aligned
+// 16-byte read takes a quarter of the shared-memory wavefronts of four
+// element reads at a 16-byte lane stride.  Generic form: element by element.
+template <typename S, int V> struct CellLoader {
+    static __device__ __forceinline__ void load(const S *p, typename StorageTraits<S>::C (&out)[V])
+    {
+#pragma unroll
+        for (int v = 0; v < V; ++v) out[v] = load_c<S>(p[v]);
+    }
+};
+template <> struct CellLoader<float, 4> {
+    static __device__ __forceinline__ void load(const float *p, float (&out)[4])
+    {
+        const unsigned mis = (unsigned)reinterpret_cast<uintptr_t>(p) & 15u;
+        if (mis == 0) {
+            const float4 q = *reinterpret_cast<const float4 *>(p);
+            out[0] = q.x, out[1] = q.y, out[2] = q.z, out[3] = q.w;
+        } else if ((mis & 7u) == 0) {
+            const float2 q0 = reinterpret_cast<const float2 *>(p)[0];
+            const float2 q1 = reinterpret_cast<const float2 *>(p)[1];
+            out[0] = q0.x, out[1] = q0.y, out[2] = q1.x, out[3] = q1.y;
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) out[v] = p[v];
+        }
+    }
+};
+template <int V> struct CellLoader<double, V> {
+    static __device__ __forceinline__ void load(const double *p, double (&out)[V])
+    {
+        if (V % 2 == 0 && ((unsigned)reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+#pragma unroll
+            for (int i = 0; i < V / 2; ++i) {
+                const double2 q = reinterpret_cast<const double2 *>(p)[i];
+                out[2 * i] = q.x, out[2 * i + 1] = q.y;
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) out[v] = p[v];
+        }
+    }
+};
+template <typename S, int V>
+__device__ __forceinline__ void load_cells(const S *p, typename StorageTraits<S>::C (&out)[V])
+{
+    CellLoader<S, V>::load(p, out);
+}
+
 template <typename S>
 __device__ __forceinline__ S to_storage(typename StorageTraits<S>::C v)
 {

@@ -63,12 +63,16 @@ struct Sweep3DGeom {
     static constexpr int ROWBUF = TX + A;        // TMA box per row
     static constexpr int ROW_BYTES = ((ROWBUF * (int)sizeof(S) + 127) / 128) * 128;
     static constexpr int SLOT_BYTES = TY * ROW_BYTES;
-    static constexpr int PF = PREFETCH_ROWS;                       // planes in flight ahead
     // box edge tiles re-read halo cells of planes up to bT*R behind
     static constexpr int KEEP = SHAPE == SH_BOX ? BT * R : 0;
-    static constexpr int D = PF + KEEP + 1;                        // ring depth (planes)
     using C = typename StorageTraits<S>::C;
     static constexpr int XB_BYTES = 2 * TY * TX * (int)sizeof(C);  // y-exchange, double buffered
+    // Planes in flight ahead of the consumer: as many as shared memory holds,
+    // between PREFETCH_ROWS and 6 (one CTA per SM keeps only this CTA's
+    // copies in flight, so a deeper ring hides more of the DRAM latency).
+    static constexpr int PF_FIT = (232448 - 128 - XB_BYTES) / (SLOT_BYTES + NW * 8) - KEEP - 1;
+    static constexpr int PF = PF_FIT > 6 ? 6 : (PF_FIT < PREFETCH_ROWS ? PREFETCH_ROWS : PF_FIT);
+    static constexpr int D = PF + KEEP + 1;                        // ring depth (planes)
     static constexpr int SMEM_BYTES = D * SLOT_BYTES + XB_BYTES + D * NW * 8 + 128;
     static_assert(SMEM_BYTES <= 232448, "shared memory per CTA exceeds 227 KB");
     static_assert(TX - 2 * BT * R >= 8 && TY - 2 * BT * R >= 2, "tile too small for bT*R");
@@ -137,10 +141,12 @@ __global__ void __launch_bounds__(NW * 32, 1)
     auto issue_plane = [&](int p, int s) {
         if (lane == 0) mbar_expect_tx(&bars[s * NW + warp], RW * G::ROWBUF * (int)sizeof(S));
         __syncwarp();
+        // No proxy fence before the copy: the slot's previous rows were read
+        // by this warp only, and those reads completed (their values were
+        // used) iterations before the slot is refilled.
         if (lane < RW) {
             const int row = warp * RW + lane;
             const int lin = (p * py + yb + row) * px + x0;
-            fence_proxy_async();
             tma_load_1d(ring + s * G::SLOT_BYTES + row * G::ROW_BYTES, &tmap, lin & ~(A - 1),
                         &bars[s * NW + warp]);
         }
@@ -195,9 +201,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
         if (have && ok) {
 #pragma unroll
             for (int r = 0; r < RW; ++r) {
-                const S *src = cells_in_slot(i, cs, r);
-#pragma unroll
-                for (int v = 0; v < V; ++v) cell[r][v] = load_c<S>(src[v]);
+                load_cells<S, V>(cells_in_slot(i, cs, r), cell[r]);
             }
         } else {
 #pragma unroll
