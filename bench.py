@@ -632,7 +632,7 @@ def run_batch(args, rank, world, local):
           for i, g in enumerate(grids)]
     ys = [torch.empty_like(x) for x in xs]
     with an5d.Batch(grids) as b:
-        info = b.tune(stream)
+        info = b.tune(stream, xs, ys)
         for _ in range(args.warmup):
             b.run(xs, ys, stream)
         torch.cuda.synchronize()
@@ -654,9 +654,14 @@ def run_batch(args, rank, world, local):
     passes_bytes = 0.0
     bt_of = {(STAR, 1): info["class_bt"][0], (STAR, 2): info["class_bt"][1],
              (BOX, 1): info["class_bt"][2], (BOX, 2): info["class_bt"][3]}
+    menu = {1: (8, 4, 1), 2: (4, 2, 1)}   # built degrees per radius, largest first
     for g in grids:
         bt = bt_of[(g[0], g[1])]
-        passes = g[5] // bt + g[5] % bt
+        left, passes = g[5] % bt, g[5] // bt   # remainder split greedily over smaller degrees
+        for m in menu[g[1]]:
+            if m < bt:
+                passes += left // m
+                left %= m
         passes_bytes += passes * g[3] * g[4] * 8.0
     t_hbm = passes_bytes / (float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) * 1e9)
     line = {"mode": "batch", "metric": "GCell-updates/s", "value": cells / (ms * 1e-3) / 1e9,

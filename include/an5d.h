@@ -282,9 +282,14 @@ typedef struct {
 an5d_batch_plan *an5d_batch_plan_create(int n, const an5d_grid_desc *descs);
 
 /* Pick each class's degree among the built ones {1,4,8} (radius 1) and
- * {1,2,4} (radius 2) by timing a 1024^2 grid of the class (Section 5.3's
- * tuning, per stencil class).  Synchronous. */
+ * {1,2,4} (radius 2) by timing whole runs of the batch (Section 5.3's
+ * tuning by measurement; coordinate descent over the classes, at most two
+ * sweeps).  an5d_batch_tune runs on temporary zero-filled buffers of every
+ * grid (allocated and freed here); an5d_batch_tune_run on the caller's ins
+ * and outs (same contract as an5d_batch_run; outs are overwritten).
+ * Synchronous. */
 int an5d_batch_tune(an5d_batch_plan *bp, void *stream);
+int an5d_batch_tune_run(an5d_batch_plan *bp, const void *const *ins, void *const *outs, void *stream);
 
 /* Force the degree of each class (class_bt[4], values from the built menu). */
 int an5d_batch_set_degrees(an5d_batch_plan *bp, const int *class_bt);

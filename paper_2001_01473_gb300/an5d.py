@@ -141,6 +141,8 @@ def load(path: str = LIB_PATH):
     L.an5d_batch_plan_create.restype = P
     L.an5d_batch_tune.argtypes = [P, P]
     L.an5d_batch_tune.restype = I
+    L.an5d_batch_tune_run.argtypes = [P, P, P, P]
+    L.an5d_batch_tune_run.restype = I
     L.an5d_batch_set_degrees.argtypes = [P, P]
     L.an5d_batch_set_degrees.restype = I
     L.an5d_batch_run.argtypes = [P, P, P, P]
@@ -430,6 +432,14 @@ def an5d_batch_tune(bp: int, stream=None) -> int:
     return _bcheck(load().an5d_batch_tune(bp, _stream(stream)))
 
 
+def an5d_batch_tune_run(bp: int, ins, outs, stream=None) -> int:
+    n = len(ins)
+    pi = (ctypes.c_void_p * n)(*[_ptr(x) for x in ins])
+    po = (ctypes.c_void_p * n)(*[_ptr(x) for x in outs])
+    return _bcheck(load().an5d_batch_tune_run(bp, ctypes.cast(pi, ctypes.c_void_p),
+                                              ctypes.cast(po, ctypes.c_void_p), _stream(stream)))
+
+
 def an5d_batch_set_degrees(bp: int, class_bt) -> int:
     a = (ctypes.c_int * 4)(*[int(x) for x in class_bt])
     return _bcheck(load().an5d_batch_set_degrees(bp, ctypes.cast(a, ctypes.c_void_p)))
@@ -464,8 +474,13 @@ class Batch:
         self.grids = list(grids)
         self.handle, self._keep = an5d_batch_plan_create(self.grids)
 
-    def tune(self, stream=None) -> dict:
-        an5d_batch_tune(self.handle, stream)
+    def tune(self, stream=None, ins=None, outs=None) -> dict:
+        """Tune the degrees by timing whole runs; on (ins, outs) when given
+        (outs are overwritten), else on temporary buffers."""
+        if ins is not None:
+            an5d_batch_tune_run(self.handle, ins, outs, stream)
+        else:
+            an5d_batch_tune(self.handle, stream)
         return self.info()
 
     def set_degrees(self, class_bt) -> None:

@@ -43,7 +43,8 @@ struct alignas(64) BatchGrid {
     CUtensorMap map[3];   // 1D maps over in, out, scratch
     float *buf[3];        // in (never written), out, scratch
     int pitch, ny, nx, radius, cls;
-    int bt, full, rem, passes;  // degree, full-degree passes, remainder (degree-1 passes), total
+    int bt, full, rem, passes;  // degree, full-degree passes, remainder passes, total
+    int rdeg[8];                // degrees of the remainder passes (T mod bT split over the menu)
     int lead;                   // bT*R: tiles start this far left of their compute region
     int stride, tiles_x, hsn, nsb;
     int counter_base;
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32)
         }
         // the neighbours' stores (generic proxy) before this warp's TMA reads (async proxy)
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        const int deg = w.pass < g.full ? g.bt : 1;
+        const int deg = w.pass < g.full ? g.bt : g.rdeg[w.pass - g.full];
         const int np = g.passes;
         const int src = w.pass == 0 ? 0 : (((np - w.pass) % 2 == 0) ? 1 : 2);
         float *dst = g.buf[((np - 1 - w.pass) % 2 == 0) ? 1 : 2];
@@ -289,7 +290,14 @@ static void batch_layout(an5d_batch_plan *bp)
         int bt = bp->class_bt[g.cls];
         g.bt = bt;
         g.full = (int)(d.T / bt);
-        g.rem = (int)(d.T % bt);
+        // the remaining T mod bT steps, greedily in the largest built degrees
+        int left = (int)(d.T % bt);
+        g.rem = 0;
+        for (int i = BATCH_MENU - 1; i >= 0; --i)
+            while (batch_menu(g.cls, i) < bt && left >= batch_menu(g.cls, i)) {
+                g.rdeg[g.rem++] = batch_menu(g.cls, i);
+                left -= batch_menu(g.cls, i);
+            }
         g.passes = g.full + g.rem;
         g.lead = bt * R;
         g.stride = 32 * CELLS_PER_LANE - 2 * bt * R;
@@ -308,12 +316,13 @@ static void batch_layout(an5d_batch_plan *bp)
     // running at the same time share the same code (each class and degree is
     // a separate, fully unrolled instantiation).  An item's dependencies (the
     // same grid, pass p - 1) come earlier in the queue.
+    auto degree_at = [](const BatchGrid &g, int p) { return p < g.full ? g.bt : g.rdeg[p - g.full]; };
     for (int p = 0; p < max_passes; ++p)
         for (int cls = 0; cls < BATCH_CLASSES; ++cls)
-            for (int full = 1; full >= 0; --full)
+            for (int m = BATCH_MENU - 1; m >= 0; --m)
                 for (int i = 0; i < bp->n; ++i) {
                     const BatchGrid &g = bp->grids[i];
-                    if (p >= g.passes || g.cls != cls || (p < g.full) != (full == 1)) continue;
+                    if (p >= g.passes || g.cls != cls || degree_at(g, p) != batch_menu(cls, m)) continue;
                     for (int sb = 0; sb < g.nsb; ++sb)
                         for (int xt = 0; xt < g.tiles_x; ++xt) bp->items.push_back(BatchItem{i, xt, sb, p});
                 }
@@ -448,52 +457,94 @@ extern "C" int an5d_batch_info(const an5d_batch_plan *bp, an5d_batch_info_t *inf
 
 // Per-class degree from the built menu, timed on a 1024^2 grid of the
 // class with the single-grid plan (same warp-tile code).
+// Time one run of the whole batch (after one untimed run of the same layout).
+static int batch_time(an5d_batch_plan *bp, const void *const *ins, void *const *outs, cudaStream_t st,
+                      float *ms)
+{
+    if (int s = an5d_batch_run(bp, ins, outs, st)) return s;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    int s = an5d_batch_run(bp, ins, outs, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == AN5D_OK) s = an5d_batch_status(bp);
+    return s;
+}
+
+extern "C" int an5d_batch_tune_run(an5d_batch_plan *bp, const void *const *ins, void *const *outs,
+                                   void *stream)
+{
+    if (!bp || !ins || !outs) return bfail(AN5D_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    bool present[BATCH_CLASSES] = {false, false, false, false};
+    for (int i = 0; i < bp->n; ++i) present[batch_cls(bp->descs[i].shape, bp->descs[i].radius)] = true;
+    int best[BATCH_CLASSES];
+    for (int c = 0; c < BATCH_CLASSES; ++c) best[c] = bp->class_bt[c];
+    float t_best = 0;
+    if (int s = batch_time(bp, ins, outs, st, &t_best)) return s;
+    // coordinate descent over the classes' degrees, timing the whole batch
+    // (the degrees interact through the shared queue, so a class is not tuned
+    // on a grid of its own)
+    for (int sweep = 0; sweep < 2; ++sweep) {
+        bool changed = false;
+        for (int c = 0; c < BATCH_CLASSES; ++c) {
+            if (!present[c]) continue;
+            for (int m = 0; m < BATCH_MENU; ++m) {
+                int trial[BATCH_CLASSES];
+                for (int k = 0; k < BATCH_CLASSES; ++k) trial[k] = best[k];
+                trial[c] = batch_menu(c, m);
+                if (trial[c] == best[c]) continue;
+                if (int s = an5d_batch_set_degrees(bp, trial)) return s;
+                float t = 0;
+                if (int s = batch_time(bp, ins, outs, st, &t)) return s;
+                if (t < t_best) {
+                    t_best = t;
+                    best[c] = trial[c];
+                    changed = true;
+                }
+            }
+        }
+        if (!changed) break;
+    }
+    return an5d_batch_set_degrees(bp, best);
+}
+
 extern "C" int an5d_batch_tune(an5d_batch_plan *bp, void *stream)
 {
     if (!bp) return bfail(AN5D_ERR_INVALID_ARG, "NULL plan");
-    int best_bt[BATCH_CLASSES];
-    for (int c = 0; c < BATCH_CLASSES; ++c) best_bt[c] = bp->class_bt[c];
-    for (int c = 0; c < BATCH_CLASSES; ++c) {
-        int gi = -1;
-        for (int i = 0; i < bp->n && gi < 0; ++i)
-            if (batch_cls(bp->descs[i].shape, bp->descs[i].radius) == c) gi = i;
-        if (gi < 0) continue;
-        const an5d_grid_desc &d = bp->descs[gi];
-        const int64_t dims[2] = {1024, 1024};
-        an5d_plan *p = an5d_plan_create(2, d.shape, d.radius, d.coeffs, AN5D_F32, dims);
-        if (!p) return bfail(an5d_last_status(), an5d_last_error());
-        void *a = nullptr, *b = nullptr;
-        const size_t bytes = (size_t)(1024 + 2 * d.radius) * (1024 + 2 * d.radius) * 4;
-        cudaMalloc(&a, bytes);
-        cudaMalloc(&b, bytes);
-        cudaMemsetAsync(a, 0, bytes, (cudaStream_t)stream);
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        double best = 1e30;
-        for (int i = 0; i < BATCH_MENU; ++i) {
-            const int bt = batch_menu(c, i);
-            if (an5d_plan_set_config(p, bt, 256)) continue;
-            const int64_t T = 8 * 8;
-            an5d_run(p, a, b, T, stream);
-            cudaEventRecord(e0, (cudaStream_t)stream);
-            an5d_run(p, a, b, T, stream);
-            cudaEventRecord(e1, (cudaStream_t)stream);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                best_bt[c] = bt;
-            }
+    // temporary zero-filled inputs and outputs of every grid's padded size
+    std::vector<void *> bufs(2 * (size_t)bp->n, nullptr);
+    int s = AN5D_OK;
+    for (int i = 0; i < bp->n && s == AN5D_OK; ++i) {
+        const size_t bytes = (size_t)bp->grids[i].pitch * (bp->grids[i].ny + 2 * bp->grids[i].radius) * 4;
+        for (int k = 0; k < 2 && s == AN5D_OK; ++k) {
+            if (cudaMalloc(&bufs[2 * i + k], bytes) != cudaSuccess)
+                s = bfail(AN5D_ERR_OOM, "batch tune: buffers");
+            else
+                cudaMemsetAsync(bufs[2 * i + k], 0, bytes, (cudaStream_t)stream);
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        cudaFree(a);
-        cudaFree(b);
-        an5d_plan_destroy(p);
     }
-    return an5d_batch_set_degrees(bp, best_bt);
+    if (s == AN5D_OK) {
+        std::vector<const void *> ins(bp->n);
+        std::vector<void *> outs(bp->n);
+        for (int i = 0; i < bp->n; ++i) ins[i] = bufs[2 * i], outs[i] = bufs[2 * i + 1];
+        s = an5d_batch_tune_run(bp, ins.data(), outs.data(), stream);
+    }
+    cudaDeviceSynchronize();
+    for (void *b : bufs) cudaFree(b);
+    // the captured graph refers to the freed buffers: force a new capture
+    if (bp->graph) {
+        cudaGraphExecDestroy(bp->graph);
+        bp->graph = nullptr;
+    }
+    bp->last_in.clear();
+    bp->last_out.clear();
+    return s;
 }
 
 extern "C" int an5d_batch_run(an5d_batch_plan *bp, const void *const *ins, void *const *outs, void *stream)

@@ -100,3 +100,19 @@ def test_batch_full_config_vs_single_grid_path():
         if not torch.equal(ref, ys[i]):
             bad.append(i)
     assert not bad, (bad[:10], info)
+
+
+def test_batch_tune_on_caller_buffers_then_oracle():
+    """Tuning on the caller's buffers (whole-batch timing) leaves a plan whose
+    result is still every grid's oracle result; remainders T mod bT are split
+    over the built degrees."""
+    import torch
+    grids = _grids_from(SMALL, seed0=300)
+    with an5d.Batch(grids) as b:
+        xs, ys = _inputs(grids, seed0=900)
+        info = b.tune(None, xs, ys)
+        assert all(d in (1, 2, 4, 8) for d in info["class_bt"])
+        b.run(xs, ys)
+        torch.cuda.synchronize()
+        assert b.status() == 0, an5d.an5d_batch_last_error()
+    _check_vs_oracle(grids, xs, ys)
