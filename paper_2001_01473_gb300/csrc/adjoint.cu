@@ -83,60 +83,129 @@ template <int SHAPE, int R> __host__ __device__ constexpr int off_dx(int k)
     return (k - 1) % 2 == 0 ? i : 0;
 }
 
-constexpr int CORR_BLOCKS = 2048;  // at most; a grid uses corr_blocks(cells) of them
+constexpr int CORR_BLOCKS = 2048;  // at most; a grid uses corr_blocks(ny, nx) of them
 constexpr int CORR_THREADS = 256;
 
-// Fixed partition of a grid's cells for the coefficient reduction: at least
-// 16 cells per thread, at most CORR_BLOCKS blocks.  Depends only on the grid.
-__host__ __device__ inline int corr_blocks(int64_t cells)
+// Fixed partition of a grid for the coefficient reduction: column groups of
+// CORR_THREADS columns times bands of about 64 rows, at most CORR_BLOCKS
+// blocks.  Depends only on the grid, so the reduction order is fixed.
+__host__ __device__ inline void corr_split(int ny, int nx, int *ncx, int *nby)
 {
-    const int64_t b = (cells + (int64_t)CORR_THREADS * 16 - 1) / ((int64_t)CORR_THREADS * 16);
-    return (int)(b < 1 ? 1 : (b > CORR_BLOCKS ? CORR_BLOCKS : b));
+    int cx = (nx + CORR_THREADS - 1) / CORR_THREADS;
+    if (cx > CORR_BLOCKS) cx = CORR_BLOCKS;
+    int by = (ny + 63) / 64;
+    if (by > CORR_BLOCKS / cx) by = CORR_BLOCKS / cx;
+    *ncx = cx;
+    *nby = by < 1 ? 1 : by;
+}
+__host__ __device__ inline int corr_blocks(int ny, int nx)
+{
+    int cx, by;
+    corr_split(ny, nx, &cx, &by);
+    return cx * by;
 }
 
-// part[b * n + k] += sum over block b's cells of g[p] * u[p + o_k] (interior p).
-// Each block owns its slots and launches on one stream are ordered, so the
-// accumulation over steps is deterministic.
+// part[b * n + k] += sum over block b's cells of g[p] * u[p + o_k] (interior
+// p).  Block b owns a band of rows of a column group; each thread walks down
+// its columns keeping the (2R+1) x (2R+1) neighbourhood of u in registers (a
+// ring of rows indexed by row mod 2R+1, so every index is static), which
+// reads 2R+2 values per cell instead of one per offset.  Each block owns its
+// slots and launches on one stream are ordered: the accumulation over steps
+// is deterministic.
+// The (g_{t+1}, u_t) pairs of the steps of one block.
+struct CorrSteps {
+    const float *g[ADJ_MAX_BT];
+    const float *u[ADJ_MAX_BT];
+    int n;
+};
+
 template <int SHAPE, int R>
 __global__ void __launch_bounds__(CORR_THREADS)
-    corr_kernel(const float *__restrict__ g, const float *__restrict__ u, int ny, int nx, double *part)
+    corr_kernel(const CorrSteps steps, int ny, int nx, double *part)
 {
     constexpr int N = NCoeff2<SHAPE, R>::value;
+    constexpr int P = 2 * R + 1;
     const int pitch = nx + 2 * R;
-    const int64_t cells = (int64_t)ny * nx;
+    int ncx, nby;
+    corr_split(ny, nx, &ncx, &nby);
+    const int cx = blockIdx.x % ncx, by = blockIdx.x / ncx;
+    // bands start on multiples of P, so the ring slot of row y is (y - y0) mod P
+    const int rpb = ((ny + nby - 1) / nby + P - 1) / P * P;
+    const int y0 = by * rpb, y1 = min(ny, y0 + rpb);
+    constexpr int NWARP = CORR_THREADS / 32;
+    __shared__ double wsum[NWARP][N];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int step = 0; step < steps.n; ++step) {
+    const float *__restrict__ g = steps.g[step];
+    const float *__restrict__ u = steps.u[step];
     float acc[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) acc[k] = 0.f;
-    for (int64_t q = blockIdx.x * (int64_t)CORR_THREADS + threadIdx.x; q < cells;
-         q += (int64_t)gridDim.x * CORR_THREADS) {
-        const int y = (int)(q / nx) + R, x = (int)(q % nx) + R;
-        const int64_t p = (int64_t)y * pitch + x;
-        const float gv = g[p];
+    for (int x = cx * CORR_THREADS + threadIdx.x; x < nx && y0 < y1; x += ncx * CORR_THREADS) {
+        // w[s][j]: u at interior row y0 + m (m mod P = s) and column x + j - R
+        const float *ucol = u + R + x;                        // padded column x + R
+        const float *gcol = g + (int64_t)R * pitch + R + x;   // interior cell (0, x)
+        float w[P][P];
 #pragma unroll
-        for (int k = 0; k < N; ++k)
-            acc[k] = __fmaf_rn(gv, u[p + off_dy<SHAPE, R>(k) * pitch + off_dx<SHAPE, R>(k)], acc[k]);
-    }
-    __shared__ double red[CORR_THREADS];
-    for (int k = 0; k < N; ++k) {
-        red[threadIdx.x] = (double)acc[k];
-        __syncthreads();
-        for (int s = CORR_THREADS / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
+        for (int d = 0; d < 2 * R; ++d) {                     // rows y0 - R .. y0 + R - 1
+            const float *row = ucol + (int64_t)(y0 + d) * pitch;
+#pragma unroll
+            for (int j = 0; j < P; ++j) w[((d - R) % P + P) % P][j] = row[j - R];
         }
-        if (threadIdx.x == 0) part[blockIdx.x * N + k] += red[0];
-        __syncthreads();
+        for (int yb = y0; yb < y1; yb += P) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int y = yb + q;
+                if (y < y1) {
+                    const float *row = ucol + (int64_t)(y + 2 * R) * pitch;   // row y + R
+#pragma unroll
+                    for (int j = 0; j < P; ++j) w[(q + R) % P][j] = row[j - R];
+                    const float gv = gcol[(int64_t)y * pitch];
+#pragma unroll
+                    for (int k = 0; k < N; ++k) {
+                        const int dy = off_dy<SHAPE, R>(k), dx = off_dx<SHAPE, R>(k);
+                        acc[k] = __fmaf_rn(gv, w[((q + dy) % P + P) % P][dx + R], acc[k]);
+                    }
+                }
+            }
+        }
+    }
+    // FP64 reduction in a fixed order, per step: a shuffle tree inside each
+    // warp, then the warps' sums in warp order (acc stays in registers:
+    // every index is static)
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        double v = (double)acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL_MASK, v, o);
+        if (lane == 0) wsum[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < NWARP; ++w) v += wsum[w][threadIdx.x];
+        part[blockIdx.x * N + threadIdx.x] += v;
+    }
+    __syncthreads();  // wsum is reused by the next step
     }
 }
 
-// dc[k] = sum_b part[b * n + k], in block order.
-__global__ void corr_final(const double *__restrict__ part, int n, int blocks, double *dc)
+// dc[k] = sum_b part[b * n + k]: one block per coefficient, a fixed strided
+// split over its threads and a fixed tree (deterministic).
+__global__ void __launch_bounds__(CORR_THREADS) corr_final(const double *__restrict__ part, int n, int blocks, double *dc)
 {
-    const int k = threadIdx.x;
-    if (k >= n) return;
+    const int k = blockIdx.x;
     double s = 0.0;
-    for (int b = 0; b < blocks; ++b) s += part[b * n + k];
-    dc[k] = s;
+    for (int b = threadIdx.x; b < blocks; b += CORR_THREADS) s += part[b * n + k];
+    __shared__ double red[CORR_THREADS];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = CORR_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dc[k] = red[0];
 }
 
 // dst := src on the interior, 0 on the halo.
@@ -160,7 +229,7 @@ using namespace an5d;
 namespace {
 
 using LevelsLaunch = cudaError_t (*)(const PassDesc &, const LevelPtrs &, cudaStream_t);
-using CorrLaunch = void (*)(const float *, const float *, int, int, double *, cudaStream_t);
+using CorrLaunch = void (*)(const CorrSteps &, int, int, double *, cudaStream_t);
 
 template <int SHAPE, int R, int BT>
 cudaError_t launch_levels(const PassDesc &d, const LevelPtrs &lv, cudaStream_t st)
@@ -192,9 +261,9 @@ cudaError_t launch_levels(const PassDesc &d, const LevelPtrs &lv, cudaStream_t s
 }
 
 template <int SHAPE, int R>
-void launch_corr(const float *g, const float *u, int ny, int nx, double *part, cudaStream_t st)
+void launch_corr(const CorrSteps &steps, int ny, int nx, double *part, cudaStream_t st)
 {
-    corr_kernel<SHAPE, R><<<corr_blocks((int64_t)ny * nx), CORR_THREADS, 0, st>>>(g, u, ny, nx, part);
+    corr_kernel<SHAPE, R><<<corr_blocks(ny, nx), CORR_THREADS, 0, st>>>(steps, ny, nx, part);
 }
 
 template <int SHAPE, int R> LevelsLaunch levels_for(int bt)
@@ -318,14 +387,19 @@ extern "C" int an5d_run_adjoint(an5d_plan *plan, const void *u0, const void *gT,
             cudaError_t e = find_levels(v.shape, R, nb)(d, lv, st);
             if (e != cudaSuccess) return set_error(AN5D_ERR_CUDA, cudaGetErrorString(e));
         }
-        // 3. dL/dc += <g_{t+1}, shift_k u_t> for t = t0 .. t0+nb-1
-        for (int s2 = 0; s2 < nb; ++s2) {
-            const float *u = (const float *)(s2 == 0 ? C[m] : U[s2]);
-            corr((const float *)G[nb - 1 - s2], u, ny, nx, part, st);
+        // 3. dL/dc += <g_{t+1}, shift_k u_t> for t = t0 .. t0+nb-1 (one launch)
+        {
+            CorrSteps cs = {};
+            cs.n = nb;
+            for (int s2 = 0; s2 < nb; ++s2) {
+                cs.g[s2] = (const float *)G[nb - 1 - s2];
+                cs.u[s2] = (const float *)(s2 == 0 ? C[m] : U[s2]);
+            }
+            corr(cs, ny, nx, part, st);
         }
         std::swap(G[0], G[nb]);
     }
-    corr_final<<<1, 32, 0, st>>>(part, n, corr_blocks((int64_t)ny * nx), dc);
+    corr_final<<<n, CORR_THREADS, 0, st>>>(part, n, corr_blocks(ny, nx), dc);
     cudaMemcpyAsync(grad_u0, G[0], v.bytes, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(grad_coeffs, dc, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
