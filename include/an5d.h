@@ -172,14 +172,26 @@ void an5d_plan_destroy(an5d_plan *plan);
 int an5d_plan_config(const an5d_plan *plan, an5d_config *cfg);
 
 /* Force a configuration (bT, hsn; 0 = keep the current value).  Other
- * fields are derived.  Returns AN5D_ERR_UNSUPPORTED for a bT not built. */
+ * fields are derived.  Returns AN5D_ERR_UNSUPPORTED for a bT not built.
+ * If the plan's tile variant does not build bT, the plan returns to the
+ * default variant. */
 int an5d_plan_set_config(an5d_plan *plan, int bT, int hsn);
 
+/* Select the sweep kernel's tile variant: 0 = the default width (128 cells
+ * along x in 2D), else a tile width along x for which a variant is built
+ * (2D FP32 radius-1 star: 192 cells, 6 per lane, at bT 4-7: less overlap
+ * per tile at a lower degree).  Keeps bT and hsn; a remainder pass whose
+ * degree the variant does not build runs on the default kernel.  Returns
+ * AN5D_ERR_UNSUPPORTED if no variant of that width exists for the plan's
+ * stencil and current bT.  cfg.tile_x reports the width in use. */
+int an5d_plan_set_tile(an5d_plan *plan, int tile_x);
+
 /* Autotune (Section 5.3's "Tuned" procedure with this library's model):
- * rank every built bT and stream-block length with the analytic model,
- * time the top `topk` candidates on the plan's scratch buffers for
+ * rank every built bT and stream-block length of every tile variant with
+ * the analytic model, time each variant's top `topk` candidates on the
+ * plan's scratch buffers for
  * `T_probe` steps on `stream`, keep the fastest.  Synchronous.  Results
- * are cached per (stencil, dtype, dims, device) for the process. */
+ * are cached per (stencil, dtype, division, dims, device) for the process. */
 int an5d_plan_tune(an5d_plan *plan, int topk, int64_t T_probe, void *stream);
 
 /* Fault injection for tests of the failure path (2D plans): while enabled,

@@ -123,6 +123,8 @@ def load(path: str = LIB_PATH):
     L.an5d_plan_config.restype = I
     L.an5d_plan_set_config.argtypes = [P, I, I]
     L.an5d_plan_set_config.restype = I
+    L.an5d_plan_set_tile.argtypes = [P, I]
+    L.an5d_plan_set_tile.restype = I
     L.an5d_plan_tune.argtypes = [P, I, I64, P]
     L.an5d_plan_tune.restype = I
     L.an5d_plan_status.argtypes = [P]
@@ -289,6 +291,10 @@ def an5d_plan_set_config(plan: int, bT: int = 0, hsn: int = 0) -> int:
     return _check(load().an5d_plan_set_config(plan, int(bT), int(hsn)))
 
 
+def an5d_plan_set_tile(plan: int, tile_x: int = 0) -> int:
+    return _check(load().an5d_plan_set_tile(plan, int(tile_x)))
+
+
 def an5d_plan_tune(plan: int, topk: int = 5, T_probe: int = 20, stream=None) -> int:
     return _check(load().an5d_plan_tune(plan, int(topk), int(T_probe), _stream(stream)))
 
@@ -376,6 +382,10 @@ class Plan:
 
     def set_config(self, bT: int = 0, hsn: int = 0) -> None:
         an5d_plan_set_config(self.handle, bT, hsn)
+
+    def set_tile(self, tile_x: int = 0) -> None:
+        """Select the sweep kernel's tile variant (0 = default width)."""
+        an5d_plan_set_tile(self.handle, tile_x)
 
     def tune(self, topk: int = 5, T_probe: int = 20, stream=None) -> dict:
         an5d_plan_tune(self.handle, topk, T_probe, stream)

@@ -158,6 +158,7 @@ struct an5d_plan {
     void *stage_in = nullptr, *stage_out = nullptr;
     int bt = 1;
     int hsn = 0;
+    int tile = 0;         // tile variant of the sweep kernel (0 = default width)
     double model_gcells = 0, measured_gcells = 0;
     int bt_max = 0;
     int stall_test = 0;  // fault injection (tests only)
@@ -198,9 +199,36 @@ struct PassGeom {
     int tile_stride_x, tiles_x, tile_stride_y, tiles_y, hsn, stream_blocks, units, ctas;
 };
 
+// Kernel of degree bt in the plan's tile variant; a degree the variant does
+// not build (a remainder pass) runs on the default kernel.
+static const KernelEntry *plan_kernel(const an5d_plan *p, int bt)
+{
+    const KernelEntry *k = find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post, p->tile});
+    if (!k && p->tile) k = find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post, 0});
+    return k;
+}
+
+// Tile variants built for the plan's stencil (0, the default, first).
+static std::vector<int> tile_variants(const an5d_plan *p)
+{
+    std::vector<int> t{0};
+    for (const auto &e : registry())
+        if (e.key.ndim == p->ndim && e.key.shape == p->shape && e.key.radius == p->radius &&
+            e.key.dtype == p->dtype && e.key.post == p->post &&
+            std::find(t.begin(), t.end(), e.key.tile) == t.end())
+            t.push_back(e.key.tile);
+    std::sort(t.begin() + 1, t.end());
+    return t;
+}
+
+static bool variant_has(const an5d_plan *p, int tile, int bt)
+{
+    return find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post, tile}) != nullptr;
+}
+
 static int pass_geometry(const an5d_plan *p, int bt, int hsn_req, PassGeom *g)
 {
-    g->k = find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post});
+    g->k = plan_kernel(p, bt);
     if (!g->k)
         return fail(AN5D_ERR_UNSUPPORTED, "no kernel for ndim=%d shape=%d R=%d dtype=%d bT=%d",
                     p->ndim, p->shape, p->radius, p->dtype, bt);
@@ -283,17 +311,22 @@ static double model_for(const an5d_plan *p, int bt, int hsn)
 static void choose_default(an5d_plan *p)
 {
     double best = -1.0;
-    int bbt = 1, bh = 0;
-    for (int bt = 1; bt <= p->bt_max; ++bt) {
-        if (!find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post})) continue;
-        const int h = default_hsn(p, bt, 1);
-        const double m = model_for(p, bt, h);
-        if (m > best) {
-            best = m;
-            bbt = bt;
-            bh = h;
+    int bbt = 1, bh = 0, btile = 0;
+    for (int tile : tile_variants(p)) {
+        p->tile = tile;
+        for (int bt = 1; bt <= p->bt_max; ++bt) {
+            if (!variant_has(p, tile, bt)) continue;
+            const int h = default_hsn(p, bt, 1);
+            const double m = model_for(p, bt, h);
+            if (m > best) {
+                best = m;
+                bbt = bt;
+                bh = h;
+                btile = tile;
+            }
         }
     }
+    p->tile = btile;
     p->bt = bbt;
     p->hsn = bh;
     p->model_gcells = best;
@@ -444,10 +477,23 @@ extern "C" int an5d_plan_set_config(an5d_plan *p, int bt, int hsn)
     if (!p) return fail(AN5D_ERR_INVALID_ARG, "NULL plan");
     if (bt < 0 || hsn < 0) return fail(AN5D_ERR_INVALID_ARG, "bT and hsn must be >= 0");
     const int nbt = bt > 0 ? bt : p->bt;
-    if (!find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, nbt, p->post}))
+    if (!variant_has(p, 0, nbt))
         return fail(AN5D_ERR_UNSUPPORTED, "bT=%d is not built for this stencil", nbt);
+    if (!variant_has(p, p->tile, nbt)) p->tile = 0;  // the variant lacks this degree
     p->bt = nbt;
     p->hsn = hsn > 0 ? hsn : default_hsn(p, nbt, 1);
+    p->model_gcells = model_for(p, p->bt, p->hsn);
+    p->measured_gcells = 0.0;
+    return ok();
+}
+
+extern "C" int an5d_plan_set_tile(an5d_plan *p, int tile_x)
+{
+    if (!p) return fail(AN5D_ERR_INVALID_ARG, "NULL plan");
+    if (tile_x < 0) return fail(AN5D_ERR_INVALID_ARG, "tile_x must be >= 0");
+    if (tile_x && !variant_has(p, tile_x, p->bt))
+        return fail(AN5D_ERR_UNSUPPORTED, "no %d-wide tile variant at bT=%d for this stencil", tile_x, p->bt);
+    p->tile = tile_x;
     p->model_gcells = model_for(p, p->bt, p->hsn);
     p->measured_gcells = 0.0;
     return ok();
@@ -587,16 +633,16 @@ extern "C" int an5d_plan_status(an5d_plan *p)
 
 namespace {
 struct TuneKey {
-    int ndim, shape, radius, dtype, device;
+    int ndim, shape, radius, dtype, post, device;
     int64_t nz, ny, nx;
     bool operator<(const TuneKey &o) const
     {
-        return std::tie(ndim, shape, radius, dtype, device, nz, ny, nx) <
-               std::tie(o.ndim, o.shape, o.radius, o.dtype, o.device, o.nz, o.ny, o.nx);
+        return std::tie(ndim, shape, radius, dtype, post, device, nz, ny, nx) <
+               std::tie(o.ndim, o.shape, o.radius, o.dtype, o.post, o.device, o.nz, o.ny, o.nx);
     }
 };
 struct TuneVal {
-    int bt, hsn;
+    int bt, hsn, tile;
     double model, measured;
 };
 std::mutex g_tune_mu;
@@ -608,35 +654,44 @@ extern "C" int an5d_plan_tune(an5d_plan *p, int topk, int64_t T_probe, void *str
     if (!p) return fail(AN5D_ERR_INVALID_ARG, "NULL plan");
     if (topk < 1) topk = 1;
     if (T_probe < 1) T_probe = 1;
-    TuneKey key{p->ndim, p->shape, p->radius, p->dtype, p->device, p->nz, p->ny, p->nx};
+    TuneKey key{p->ndim, p->shape, p->radius, p->dtype, p->post, p->device, p->nz, p->ny, p->nx};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             p->bt = it->second.bt;
             p->hsn = it->second.hsn;
+            p->tile = it->second.tile;
             p->model_gcells = it->second.model;
             p->measured_gcells = it->second.measured;
             return ok();
         }
     }
     struct Cand {
-        int bt, hsn;
+        int bt, hsn, tile;
         double model;
     };
+    // the model's top k of every tile variant are timed
+    const int save_tile = p->tile;
     std::vector<Cand> cands;
-    for (int bt = 1; bt <= p->bt_max; ++bt) {
-        if (!find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post})) continue;
-        for (int waves = 1; waves <= 4; waves *= 2) {
-            const int h = default_hsn(p, bt, waves);
-            if (h <= 0) continue;
-            bool dup = false;
-            for (auto &c : cands) dup |= (c.bt == bt && c.hsn == h);
-            if (!dup) cands.push_back({bt, h, model_for(p, bt, h)});
+    for (int tile : tile_variants(p)) {
+        p->tile = tile;
+        std::vector<Cand> vc;
+        for (int bt = 1; bt <= p->bt_max; ++bt) {
+            if (!variant_has(p, tile, bt)) continue;
+            for (int waves = 1; waves <= 4; waves *= 2) {
+                const int h = default_hsn(p, bt, waves);
+                if (h <= 0) continue;
+                bool dup = false;
+                for (auto &c : vc) dup |= (c.bt == bt && c.hsn == h);
+                if (!dup) vc.push_back({bt, h, tile, model_for(p, bt, h)});
+            }
         }
+        std::sort(vc.begin(), vc.end(), [](const Cand &a, const Cand &b) { return a.model > b.model; });
+        if ((int)vc.size() > topk) vc.resize(topk);
+        cands.insert(cands.end(), vc.begin(), vc.end());
     }
-    std::sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) { return a.model > b.model; });
-    if ((int)cands.size() > topk) cands.resize(topk);
+    p->tile = save_tile;
     cudaStream_t st = (cudaStream_t)stream;
     void *a = nullptr, *b = nullptr;
     CUDA_TRY(cudaMalloc(&a, p->bytes));
@@ -651,11 +706,12 @@ extern "C" int an5d_plan_tune(an5d_plan *p, int topk, int64_t T_probe, void *str
     cudaEventCreate(&e1);
     const int save_bt = p->bt, save_hsn = p->hsn;
     double best = -1.0;
-    Cand win = cands.empty() ? Cand{save_bt, save_hsn, 0.0} : cands[0];
+    Cand win = cands.empty() ? Cand{save_bt, save_hsn, save_tile, 0.0} : cands[0];
     int status = AN5D_OK;
     for (const auto &c : cands) {
         p->bt = c.bt;
         p->hsn = c.hsn;
+        p->tile = c.tile;
         const int64_t T = std::max<int64_t>(T_probe, c.bt);
         if ((status = run_impl(p, a, b, T, st))) break;   // warm-up
         cudaEventRecord(e0, st);
@@ -677,15 +733,17 @@ extern "C" int an5d_plan_tune(an5d_plan *p, int topk, int64_t T_probe, void *str
     if (status) {
         p->bt = save_bt;
         p->hsn = save_hsn;
+        p->tile = save_tile;
         return status;
     }
     p->bt = win.bt;
     p->hsn = win.hsn;
+    p->tile = win.tile;
     p->model_gcells = win.model;
     p->measured_gcells = best;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = TuneVal{win.bt, win.hsn, win.model, best};
+        g_tune_cache[key] = TuneVal{win.bt, win.hsn, win.tile, win.model, best};
     }
     return ok();
 }
@@ -825,6 +883,7 @@ int plan_view(const an5d_plan *p, PlanView *v)
     v->n = p->n;
     v->bt = p->bt;
     v->hsn = p->hsn;
+    v->tile = p->tile;
     v->device = p->device;
     v->nz = p->nz;
     v->ny = p->ny;

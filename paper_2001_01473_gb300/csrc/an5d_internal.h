@@ -49,10 +49,11 @@ using LaunchFn = cudaError_t (*)(const PassDesc &, cudaStream_t);
 struct KernelKey {
     int ndim, shape, radius, dtype, bt;
     int post = POST_NONE;
+    int tile = 0;  // tile variant: 0 = the default kernel, else its tile width along x
     bool operator==(const KernelKey &o) const
     {
         return ndim == o.ndim && shape == o.shape && radius == o.radius && dtype == o.dtype &&
-               bt == o.bt && post == o.post;
+               bt == o.bt && post == o.post && tile == o.tile;
     }
 };
 
@@ -87,6 +88,7 @@ namespace an5d {
 // Read-only view of a plan for translation units other than the C-ABI one.
 struct PlanView {
     int ndim, shape, radius, dtype, n, bt, hsn, device;
+    int tile;              // tile variant of the chosen kernel (0 = default)
     int post;              // POST_NONE unless the plan is a division-type stencil
     int64_t nz, ny, nx, total;
     size_t bytes;

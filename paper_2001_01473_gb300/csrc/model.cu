@@ -78,7 +78,8 @@ double model_gcells(const ModelInput &m)
     // and lead-out rows (Section 3.2's redundant sub-planes).
     const double iters = m.hsn + 2.0 * m.bt * R;
     double hbm_bytes, warp_instr, fma_lanes;
-    const double V = CELLS_PER_LANE;
+    // cells per lane of the kernel: 2D tiles are one warp wide
+    const double V = m.ndim == 2 ? m.tile_x / 32.0 : CELLS_PER_LANE;
     if (m.ndim == 2) {
         const double rowbuf = m.tile_x + 16.0 / w;
         hbm_bytes = (double)m.units * iters * rowbuf * w + cells * w;

@@ -9,7 +9,9 @@
 // output rows (Section 3.2, "Division of Streaming Dimension").
 //
 // GB300 mapping (this library's design, not the paper's V100 scheme):
-//  * one warp owns one tile of 32 lanes x 4 consecutive x cells; warps never
+//  * one warp owns one tile of 32 lanes x V consecutive x cells (V = 4; a
+//    variant with V = 6 loses a smaller share of its tile to the overlap
+//    at the degrees that fit the same registers); warps never
 //    synchronise with each other: in-plane (x) neighbours travel by warp
 //    shuffles, so the paper's shared-memory neighbour exchange and its
 //    double buffering (Section 3.2) are not needed;
@@ -58,8 +60,8 @@ template <typename S, int N> struct Sweep2DArgs {
     unsigned long long post_p;             // FP32: (post_c, post_c)
 };
 
-template <typename S, int BT, int R> struct Sweep2DGeom {
-    static constexpr int V = CELLS_PER_LANE;
+template <typename S, int BT, int R, int V_ = CELLS_PER_LANE> struct Sweep2DGeom {
+    static constexpr int V = V_;  // consecutive x cells per lane
     static constexpr int P = 2 * R + 1;  // register-ring period = unroll factor
     static constexpr int A = StorageTraits<S>::ALIGN_ELEMS;
     static constexpr int TILE = 32 * V;
@@ -79,16 +81,18 @@ template <typename S, int BT, int R> struct Sweep2DGeom {
     static_assert(TILE - 2 * BT * R >= 8, "tile too narrow for bT*R");
     static_assert(R <= V, "radius must not exceed cells per lane");
     static_assert(PF <= 32, "prefetch lanes");
+    static_assert(ROWBUF <= 256, "one TMA box holds at most 256 elements per dimension");
 };
 
 // CTAs per SM the register budget is sized for: the level rings need
-// bT * (2R+1) * 4 values per thread, plus registers for addressing,
+// bT * (2R+1) * V values per thread, plus registers for addressing,
 // accumulators and shuffled neighbours.
 // Box stencils keep the arriving row and its shifted copies live as well.
-template <typename S, int SHAPE, int BT, int R, int MODE> struct Sweep2DOccupancy {
+template <typename S, int SHAPE, int BT, int R, int MODE, int V_ = CELLS_PER_LANE>
+struct Sweep2DOccupancy {
     static constexpr int words =
         (int)(sizeof(typename StorageTraits<S>::C) / 4) * (MODE == MODE_DOT2 ? 2 : 1);
-    static constexpr int regs = BT * (2 * R + 1) * CELLS_PER_LANE * words +
+    static constexpr int regs = BT * (2 * R + 1) * V_ * words +
                                 (SHAPE == SH_STAR ? 34 + 10 * R + 20 * (words - 1)
                                                     : 40 + 2 * (2 * R + 1) * (2 * R + 1) + 8 * R * words);
     static constexpr int raw = 65536 / (WARPS_PER_CTA * 32 * (((regs + 7) / 8) * 8));
@@ -122,7 +126,7 @@ struct Tile2D {
 // is the reciprocal (post_p: the pair (post_c, post_c)).  Returns false if a
 // bounded wait gave up.
 template <int SHAPE, int R, int BT, typename S, int MODE, bool PACK, typename CF, typename CP,
-          bool LEVELS = false, bool RAW = false, int POST = POST_NONE>
+          bool LEVELS = false, bool RAW = false, int POST = POST_NONE, int V_ = CELLS_PER_LANE>
 __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap *tmap, S *const dst,
                                              int *const status, unsigned char *const ring,
                                              const CF &cf, const CP &cp, S *const *lvl = nullptr,
@@ -130,7 +134,7 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
                                              const f2_t post_p = 0)
 {
     using C = typename StorageTraits<S>::C;
-    using G = Sweep2DGeom<S, BT, R>;
+    using G = Sweep2DGeom<S, BT, R, V_>;
     constexpr int V = G::V;
     constexpr int P = G::P;
     constexpr int D = G::D;
@@ -693,12 +697,12 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
     return true;
 }
 
-template <int SHAPE, int R, int BT, typename S, int MODE, int POST>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE, BT, R, MODE>::value))
+template <int SHAPE, int R, int BT, typename S, int MODE, int POST, int V_>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE, BT, R, MODE, V_>::value))
     sweep2d_kernel(const __grid_constant__ CUtensorMap tmap,
                    const Sweep2DArgs<S, NCoeff2<SHAPE, R>::value> a)
 {
-    using G = Sweep2DGeom<S, BT, R>;
+    using G = Sweep2DGeom<S, BT, R, V_>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * WARPS_PER_CTA + warp;
@@ -721,18 +725,18 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
     tg.stall = a.stall_test && gw == 0;
     unsigned char *const smem_al = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
-    sweep2d_tile<SHAPE, R, BT, S, MODE, true, decltype(a.k.c), decltype(a.kp.c), false, false, POST>(
+    sweep2d_tile<SHAPE, R, BT, S, MODE, true, decltype(a.k.c), decltype(a.kp.c), false, false, POST, V_>(
         tg, &tmap, a.dst, a.status, smem_al + warp * G::WARP_BYTES, a.k.c, a.kp.c, nullptr, a.post_c,
         a.post_p);
 }
 
 // Host-side launcher of one instantiation.
-template <int SHAPE, int R, int BT, typename S, int MODE, int POST>
+template <int SHAPE, int R, int BT, typename S, int MODE, int POST, int V_>
 cudaError_t launch_sweep2d(const PassDesc &d, cudaStream_t st)
 {
     constexpr int N = NCoeff2<SHAPE, R>::value;
     using C = typename StorageTraits<S>::C;
-    using G = Sweep2DGeom<S, BT, R>;
+    using G = Sweep2DGeom<S, BT, R, V_>;
     Sweep2DArgs<S, N> a;
     a.dst = static_cast<S *>(d.dst);
     a.status = d.status;
@@ -758,7 +762,7 @@ cudaError_t launch_sweep2d(const PassDesc &d, cudaStream_t st)
         memcpy(&u, &f, 4);
         a.post_p = ((unsigned long long)u << 32) | u;
     }
-    auto fn = sweep2d_kernel<SHAPE, R, BT, S, MODE, POST>;
+    auto fn = sweep2d_kernel<SHAPE, R, BT, S, MODE, POST, V_>;
     if (G::CTA_BYTES > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              G::CTA_BYTES);
@@ -768,14 +772,16 @@ cudaError_t launch_sweep2d(const PassDesc &d, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int SHAPE, int R, int BT, typename S, int MODE, int POST = POST_NONE>
+// V_ = cells per lane: the default width registers as tile variant 0, a
+// wider one under its tile width (32 * V_ cells).
+template <int SHAPE, int R, int BT, typename S, int MODE, int POST = POST_NONE, int V_ = CELLS_PER_LANE>
 KernelEntry entry2d(int dtype)
 {
-    using G = Sweep2DGeom<S, BT, R>;
+    using G = Sweep2DGeom<S, BT, R, V_>;
     KernelEntry e;
-    e.key = KernelKey{2, SHAPE, R, dtype, BT, POST};
-    e.launch = &launch_sweep2d<SHAPE, R, BT, S, MODE, POST>;
-    e.func = reinterpret_cast<const void *>(&sweep2d_kernel<SHAPE, R, BT, S, MODE, POST>);
+    e.key = KernelKey{2, SHAPE, R, dtype, BT, POST, V_ == CELLS_PER_LANE ? 0 : G::TILE};
+    e.launch = &launch_sweep2d<SHAPE, R, BT, S, MODE, POST, V_>;
+    e.func = reinterpret_cast<const void *>(&sweep2d_kernel<SHAPE, R, BT, S, MODE, POST, V_>);
     e.threads = WARPS_PER_CTA * 32;
     e.smem_bytes = G::CTA_BYTES;
     e.tile_x = G::TILE;

@@ -38,6 +38,17 @@ KERNELS_2D = [
     (BOX, 1, range(1, 7), "float", "MODE_DOT2", "DT_F32C"),
 ]
 
+# Wider 2D tile variants: (shape, radius, bT range, storage, mode, dtype,
+# cells per lane).  A lane of the default kernel owns 4 cells, so a warp
+# tile is 128 cells wide and loses 2 bT R of them to the overlap; 6 cells
+# per lane lose a smaller share at the degrees whose level rings still fit
+# the same register budget.  (8 per lane would need a 260-element TMA row
+# box, above the 256-element limit of one box.)  The tuner times them
+# beside the default kernels.
+KERNELS_2D_WIDE = [
+    (STAR, 1, range(4, 8), "float", "MODE_PLAIN", "DT_F32", 6),
+]
+
 
 # 3D: (shape, radius, bT range, storage, mode, dtype, warps per CTA).  A CTA
 # tile is (2 * warps) rows by 128 cells; the register rings of the whole
@@ -108,6 +119,9 @@ def instantiations():
     for shape, r, bts, s, mode, dt in KERNELS_2D:
         for bt in bts:
             yield "sweep2d.cuh", f"entry2d<{shape}, {r}, {bt}, {s}, {mode}>({dt})"
+    for shape, r, bts, s, mode, dt, v in KERNELS_2D_WIDE:
+        for bt in bts:
+            yield "sweep2d.cuh", f"entry2d<{shape}, {r}, {bt}, {s}, {mode}, POST_NONE, {v}>({dt})"
     for shape, r, bts, s, mode, dt, nw in KERNELS_3D:
         v, rw = geom3d(shape, r, s)
         for bt in bts:

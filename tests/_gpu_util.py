@@ -23,7 +23,9 @@ def oracle_run(ndim, shape, R, c, dtype, dims, u0, T):
     raise ValueError(dtype)
 
 
-def gpu_run(ndim, shape, R, c, dtype, dims, u0, T, bT=None, hsn=0, plan=None):
+def gpu_run(ndim, shape, R, c, dtype, dims, u0, T, bT=None, hsn=0, plan=None, tile=0):
+    """Run through the C ABI.  With bT or hsn given, the plan is forced to that
+    configuration on tile variant `tile` (0 = the default kernel width)."""
     import torch
     own = plan is None
     if own:
@@ -31,6 +33,7 @@ def gpu_run(ndim, shape, R, c, dtype, dims, u0, T, bT=None, hsn=0, plan=None):
     try:
         if bT is not None or hsn:
             plan.set_config(bT or 0, hsn)
+            plan.set_tile(tile)
         x = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
         y = torch.empty_like(x)
         plan.run(x, y, T)
