@@ -253,15 +253,15 @@ def kernel_source_digest() -> str:
     return h.hexdigest()[:12]
 
 
-def committed_traffic(workload: str, bt: int):
+def committed_traffic(workload: str, bt: int, tile: int):
     """dram bytes per launch of the sweep kernel recorded under profiles/ for
-    this workload and degree, if taken on the current kernel source."""
+    this workload, degree and tile width, if taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "sweep2d_traffic.md")
     if not os.path.exists(p):
         return None
     digest = kernel_source_digest()
-    pat = re.compile(r"^\|\s*%s\s*\|\s*%d\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]+)\s*\|"
-                     % (re.escape(workload), bt))
+    pat = re.compile(r"^\|\s*%s\s*\|\s*%d\s*\|\s*%d\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9.eE+]+)\s*\|"
+                     r"\s*([0-9a-f]+)\s*\|" % (re.escape(workload), bt, tile))
     with open(p) as f:
         for line in f:
             m = pat.match(line.strip())
@@ -424,7 +424,12 @@ def run_ours(args, rank, world, local):
         plan = an5d.Plan(ndim, shape, R, c, dtype, dims, divisor=DIVISOR, post=post)
     else:
         plan = an5d.Plan(ndim, shape, R, c, dtype, dims)
-    plan.tune(topk=args.topk, T_probe=args.tune_T, stream=stream)
+    if args.config:
+        fbt, fhsn, ftile = (int(v) for v in args.config.split(","))
+        plan.set_config(fbt, fhsn)
+        plan.set_tile(ftile)
+    else:
+        plan.tune(topk=args.topk, T_probe=args.tune_T, stream=stream)
     cfg = plan.config()
     bt = cfg["bT"]
     passes = T // bt + (1 if T % bt else 0)
@@ -491,7 +496,7 @@ def run_ours(args, rank, world, local):
         bound, achieved, peak, unit = "hbm", hbm_bytes_launch / launch_s / 1e9, hbm_peak, "GB/s"
     else:
         bound, achieved, peak, unit = "alu", flops_launch / launch_s / 1e12, alu_peak, "TFLOP/s"
-    traffic = committed_traffic(args.workload, bt)
+    traffic = committed_traffic(args.workload, bt, cfg["tile_x"])
     roof_gcells = cells * bt / max(t_hbm, t_alu) / 1e9
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": traffic,
@@ -499,7 +504,8 @@ def run_ours(args, rank, world, local):
                                 ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if dtype != "f64"
                                  else "in-run FP64 fma microbenchmark")),
                 "kernel": (f"box1_kernel bT={bt}" if ndim == 3 and shape == BOX and R >= 2
-                           else f"sweep{ndim}d_kernel bT={bt}"), "launches_per_step": passes,
+                           else f"sweep{ndim}d_kernel bT={bt} tile_x={cfg['tile_x']}"),
+                "launches_per_step": passes,
                 "full_degree_launches": full_passes,
                 "algorithmic_bytes_per_launch": hbm_bytes_launch,
                 "algorithmic_flops_per_launch": flops_launch,
@@ -764,6 +770,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--topk", type=int, default=6)
     ap.add_argument("--tune-T", type=int, default=40)
+    ap.add_argument("--config", default=None, metavar="BT,HSN,TILE",
+                    help="force a blocking (degree, stream-block length, tile width; 0 = default) "
+                         "instead of tuning, e.g. to profile the kernel the full-size run picks")
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", action="store_true",

@@ -236,6 +236,8 @@ cudaError_t launch_levels(const PassDesc &d, const LevelPtrs &lv, cudaStream_t s
 {
     constexpr int N = NCoeff2<SHAPE, R>::value;
     using G = Sweep2DGeom<float, BT, R>;
+    // the descriptor must describe this kernel's tile width (its TMA box too)
+    if (d.tile_stride_x != G::TILE - 2 * BT * R) return cudaErrorInvalidValue;
     Sweep2DArgs<float, N> a;
     a.dst = static_cast<float *>(d.dst);
     a.status = d.status;
@@ -371,7 +373,7 @@ extern "C" int an5d_run_adjoint(an5d_plan *plan, const void *u0, const void *gT,
         // 1. recompute u_{t0+1} .. u_{t0+nb-1} from the checkpoint
         if (nb >= 2) {
             PassDesc d;
-            if (int s = plan_fill_pass(plan, nb - 1, C[m], U[nb - 1], &d)) return s;
+            if (int s = plan_fill_pass(plan, nb - 1, 0, C[m], U[nb - 1], &d)) return s;
             LevelPtrs lv = {};
             for (int t = 1; t < nb - 1; ++t) lv.p[t] = (float *)U[t];
             cudaError_t e = find_levels(v.shape, R, nb - 1)(d, lv, st);
@@ -380,7 +382,7 @@ extern "C" int an5d_run_adjoint(an5d_plan *plan, const void *u0, const void *gT,
         // 2. transposed stencil: g_{t0+nb} -> g_{t0}, every level stored (G[j] = g_{t0+nb-j})
         {
             PassDesc d;
-            if (int s = plan_fill_pass(plan, nb, G[0], G[nb], &d)) return s;
+            if (int s = plan_fill_pass(plan, nb, 0, G[0], G[nb], &d)) return s;
             for (int k = 0; k < n; ++k) d.coeffs[k] = mc[k];
             LevelPtrs lv = {};
             for (int t = 1; t < nb; ++t) lv.p[t] = (float *)G[t];

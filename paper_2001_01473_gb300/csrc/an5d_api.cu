@@ -199,10 +199,12 @@ struct PassGeom {
     int tile_stride_x, tiles_x, tile_stride_y, tiles_y, hsn, stream_blocks, units, ctas;
 };
 
-// Kernel of degree bt in the plan's tile variant; a degree the variant does
-// not build (a remainder pass) runs on the default kernel.
-static const KernelEntry *plan_kernel(const an5d_plan *p, int bt)
+// Kernel of degree bt in tile variant `tile`, or (tile < 0) in the plan's
+// variant, where a degree the variant does not build (a remainder pass)
+// runs on the default kernel.
+static const KernelEntry *plan_kernel(const an5d_plan *p, int bt, int tile)
 {
+    if (tile >= 0) return find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post, tile});
     const KernelEntry *k = find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post, p->tile});
     if (!k && p->tile) k = find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post, 0});
     return k;
@@ -226,9 +228,9 @@ static bool variant_has(const an5d_plan *p, int tile, int bt)
     return find_kernel(KernelKey{p->ndim, p->shape, p->radius, p->dtype, bt, p->post, tile}) != nullptr;
 }
 
-static int pass_geometry(const an5d_plan *p, int bt, int hsn_req, PassGeom *g)
+static int pass_geometry(const an5d_plan *p, int bt, int hsn_req, PassGeom *g, int tile = -1)
 {
-    g->k = plan_kernel(p, bt);
+    g->k = plan_kernel(p, bt, tile);
     if (!g->k)
         return fail(AN5D_ERR_UNSUPPORTED, "no kernel for ndim=%d shape=%d R=%d dtype=%d bT=%d",
                     p->ndim, p->shape, p->radius, p->dtype, bt);
@@ -894,10 +896,10 @@ int plan_view(const an5d_plan *p, PlanView *v)
     return AN5D_OK;
 }
 
-int plan_fill_pass(const an5d_plan *p, int bt, const void *src, void *dst, PassDesc *d)
+int plan_fill_pass(const an5d_plan *p, int bt, int tile, const void *src, void *dst, PassDesc *d)
 {
     PassGeom g;
-    if (int s = pass_geometry(p, bt, p->hsn, &g)) return s;
+    if (int s = pass_geometry(p, bt, p->hsn, &g, tile)) return s;
     memset(d, 0, sizeof(*d));
     const int A = 16 / (int)elem_size(p->dtype);
     if (int s = encode_row_map(&d->tmap, src, p->dtype, p->total, g.k->tile_x + A)) return s;

@@ -95,8 +95,11 @@ struct PlanView {
     const double *coeffs;  // rounded to the compute precision
 };
 int plan_view(const an5d_plan *p, PlanView *v);
-// Pass descriptor (tensor map over src, geometry, coefficients) of degree bt.
-int plan_fill_pass(const an5d_plan *p, int bt, const void *src, void *dst, PassDesc *d);
+// Pass descriptor (tensor map over src, geometry, coefficients) of degree bt
+// for the kernels of tile variant `tile` (0 = default width, -1 = the plan's
+// own choice).  A caller that launches its own kernels with it must ask for
+// the width those kernels are built for.
+int plan_fill_pass(const an5d_plan *p, int bt, int tile, const void *src, void *dst, PassDesc *d);
 int plan_launch_pass(const an5d_plan *p, int bt, const void *src, void *dst, cudaStream_t st);
 int plan_launch_halo_copy(const an5d_plan *p, const void *src, void *dst, cudaStream_t st);
 int set_error(int status, const char *msg);

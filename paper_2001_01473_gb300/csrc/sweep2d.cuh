@@ -697,8 +697,11 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
     return true;
 }
 
-template <int SHAPE, int R, int BT, typename S, int MODE, int POST, int V_>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE, BT, R, MODE, V_>::value))
+// OCC_ > 0 fixes the CTAs per SM the registers are sized for (else the
+// Sweep2DOccupancy estimate).
+template <int SHAPE, int R, int BT, typename S, int MODE, int POST, int V_, int OCC_>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32,
+                                  (OCC_ > 0 ? OCC_ : Sweep2DOccupancy<S, SHAPE, BT, R, MODE, V_>::value))
     sweep2d_kernel(const __grid_constant__ CUtensorMap tmap,
                    const Sweep2DArgs<S, NCoeff2<SHAPE, R>::value> a)
 {
@@ -731,12 +734,14 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<S, SHAPE
 }
 
 // Host-side launcher of one instantiation.
-template <int SHAPE, int R, int BT, typename S, int MODE, int POST, int V_>
+template <int SHAPE, int R, int BT, typename S, int MODE, int POST, int V_, int OCC_>
 cudaError_t launch_sweep2d(const PassDesc &d, cudaStream_t st)
 {
     constexpr int N = NCoeff2<SHAPE, R>::value;
     using C = typename StorageTraits<S>::C;
     using G = Sweep2DGeom<S, BT, R, V_>;
+    // the descriptor must describe this kernel's tile width (its TMA box too)
+    if (d.tile_stride_x != G::TILE - 2 * BT * R) return cudaErrorInvalidValue;
     Sweep2DArgs<S, N> a;
     a.dst = static_cast<S *>(d.dst);
     a.status = d.status;
@@ -762,7 +767,7 @@ cudaError_t launch_sweep2d(const PassDesc &d, cudaStream_t st)
         memcpy(&u, &f, 4);
         a.post_p = ((unsigned long long)u << 32) | u;
     }
-    auto fn = sweep2d_kernel<SHAPE, R, BT, S, MODE, POST, V_>;
+    auto fn = sweep2d_kernel<SHAPE, R, BT, S, MODE, POST, V_, OCC_>;
     if (G::CTA_BYTES > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              G::CTA_BYTES);
@@ -774,14 +779,15 @@ cudaError_t launch_sweep2d(const PassDesc &d, cudaStream_t st)
 
 // V_ = cells per lane: the default width registers as tile variant 0, a
 // wider one under its tile width (32 * V_ cells).
-template <int SHAPE, int R, int BT, typename S, int MODE, int POST = POST_NONE, int V_ = CELLS_PER_LANE>
+template <int SHAPE, int R, int BT, typename S, int MODE, int POST = POST_NONE, int V_ = CELLS_PER_LANE,
+          int OCC_ = 0>
 KernelEntry entry2d(int dtype)
 {
     using G = Sweep2DGeom<S, BT, R, V_>;
     KernelEntry e;
     e.key = KernelKey{2, SHAPE, R, dtype, BT, POST, V_ == CELLS_PER_LANE ? 0 : G::TILE};
-    e.launch = &launch_sweep2d<SHAPE, R, BT, S, MODE, POST, V_>;
-    e.func = reinterpret_cast<const void *>(&sweep2d_kernel<SHAPE, R, BT, S, MODE, POST, V_>);
+    e.launch = &launch_sweep2d<SHAPE, R, BT, S, MODE, POST, V_, OCC_>;
+    e.func = reinterpret_cast<const void *>(&sweep2d_kernel<SHAPE, R, BT, S, MODE, POST, V_, OCC_>);
     e.threads = WARPS_PER_CTA * 32;
     e.smem_bytes = G::CTA_BYTES;
     e.tile_x = G::TILE;

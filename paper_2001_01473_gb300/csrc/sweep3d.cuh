@@ -503,6 +503,9 @@ cudaError_t launch_sweep3d(const PassDesc &d, cudaStream_t st)
     constexpr int N = NCoeff3<SHAPE, R>::value;
     using C = typename StorageTraits<S>::C;
     using G = Sweep3DGeom<S, SHAPE, BT, R, NW, V_, RW_>;
+    // the descriptor must describe this kernel's tile (its TMA box too)
+    if (d.tile_stride_x != G::TX - 2 * BT * R || d.tile_stride_y != G::TY - 2 * BT * R)
+        return cudaErrorInvalidValue;
     Sweep3DArgs<S, N> a;
     a.dst = static_cast<S *>(d.dst);
     a.status = d.status;

@@ -229,6 +229,8 @@ cudaError_t launch_box1(const PassDesc &d, cudaStream_t st)
     constexpr int N = NCoeff3<SH_BOX, R>::value;
     using C = typename StorageTraits<S>::C;
     using G = Box1Geom<S, R, NW, RW_>;
+    // the descriptor must describe this kernel's tile (one level: bT = 1)
+    if (d.tile_stride_x != G::TX - 2 * R || d.tile_stride_y != G::TY - 2 * R) return cudaErrorInvalidValue;
     Sweep3DArgs<S, N> a;
     a.dst = static_cast<S *>(d.dst);
     a.status = d.status;

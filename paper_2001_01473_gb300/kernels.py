@@ -39,14 +39,21 @@ KERNELS_2D = [
 ]
 
 # Wider 2D tile variants: (shape, radius, bT range, storage, mode, dtype,
-# cells per lane).  A lane of the default kernel owns 4 cells, so a warp
-# tile is 128 cells wide and loses 2 bT R of them to the overlap; 6 cells
-# per lane lose a smaller share at the degrees whose level rings still fit
-# the same register budget.  (8 per lane would need a 260-element TMA row
-# box, above the 256-element limit of one box.)  The tuner times them
-# beside the default kernels.
+# cells per lane, CTAs per SM the registers are sized for; 0 = estimate).
+# A lane of the default kernel owns 4 cells, so a warp tile is 128 cells
+# wide and loses 2 bT R of them to the overlap; 6 cells per lane lose a
+# smaller share at the degrees whose level rings still fit 3 CTAs per SM.
+# (8 per lane would need a 260-element TMA row box, above the 256-element
+# limit of one box.)  The tuner times them beside the default kernels.
 KERNELS_2D_WIDE = [
-    (STAR, 1, range(4, 8), "float", "MODE_PLAIN", "DT_F32", 6),
+    (STAR, 1, range(4, 7), "float", "MODE_PLAIN", "DT_F32", 6, 0),
+    (STAR, 2, range(2, 4), "float", "MODE_PLAIN", "DT_F32", 6, 3),
+    (BOX, 1, range(3, 6), "float", "MODE_PLAIN", "DT_F32", 6, 3),
+]
+# the same for division-type stencils (both forms): (shape, radius, bT
+# range, storage, dtype, cells per lane, CTAs per SM)
+KERNELS_DIV_2D_WIDE = [
+    (STAR, 1, range(4, 7), "float", "DT_F32", 6, 0),
 ]
 
 
@@ -119,9 +126,9 @@ def instantiations():
     for shape, r, bts, s, mode, dt in KERNELS_2D:
         for bt in bts:
             yield "sweep2d.cuh", f"entry2d<{shape}, {r}, {bt}, {s}, {mode}>({dt})"
-    for shape, r, bts, s, mode, dt, v in KERNELS_2D_WIDE:
+    for shape, r, bts, s, mode, dt, v, occ in KERNELS_2D_WIDE:
         for bt in bts:
-            yield "sweep2d.cuh", f"entry2d<{shape}, {r}, {bt}, {s}, {mode}, POST_NONE, {v}>({dt})"
+            yield "sweep2d.cuh", f"entry2d<{shape}, {r}, {bt}, {s}, {mode}, POST_NONE, {v}, {occ}>({dt})"
     for shape, r, bts, s, mode, dt, nw in KERNELS_3D:
         v, rw = geom3d(shape, r, s)
         for bt in bts:
@@ -132,6 +139,9 @@ def instantiations():
         for shape, r, bts, s, dt in KERNELS_DIV_2D:
             for bt in bts:
                 yield "sweep2d.cuh", f"entry2d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {post}>({dt})"
+        for shape, r, bts, s, dt, v, occ in KERNELS_DIV_2D_WIDE:
+            for bt in bts:
+                yield "sweep2d.cuh", f"entry2d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {post}, {v}, {occ}>({dt})"
         for shape, r, bts, s, dt, nw in KERNELS_DIV_3D:
             v, rw = geom3d(shape, r, s)
             for bt in bts:
