@@ -180,8 +180,9 @@ int an5d_plan_set_config(an5d_plan *plan, int bT, int hsn);
 /* Select the sweep kernel's tile variant: 0 = the default width (128 cells
  * along x in 2D), else a tile width along x for which a variant is built
  * (2D FP32: 192 cells, 6 per lane, for the radius-1 star at bT 4-6, also in
- * both division forms, the radius-2 star at bT 2-3 and the radius-1 box at
- * bT 3-5: less overlap per tile at a lower degree).  Keeps bT and hsn; a remainder pass whose
+ * both division forms, the radius-2 star at bT 2-3, the radius-3 star at
+ * bT 2 and the radius-1 box at bT 3-5: less overlap per tile at a lower
+ * degree).  Keeps bT and hsn; a remainder pass whose
  * degree the variant does not build runs on the default kernel.  Returns
  * AN5D_ERR_UNSUPPORTED if no variant of that width exists for the plan's
  * stencil and current bT.  cfg.tile_x reports the width in use. */

@@ -34,6 +34,43 @@
 
 namespace an5d {
 
+// V cells of a lane to or from the y-exchange buffer.  Each lane's cells
+// start on a 16-byte boundary there (128-byte aligned buffer, rows of
+// 32 * V cells), so whole 16-byte vectors move where V cells fill them.
+template <typename C, int V> __device__ __forceinline__ void xb_store(C *p, const C (&v)[V])
+{
+    if constexpr (std::is_same<C, float>::value && V % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < V / 4; ++i)
+            reinterpret_cast<float4 *>(p)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    } else if constexpr (std::is_same<C, double>::value && V % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < V / 2; ++i) reinterpret_cast<double2 *>(p)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) p[i] = v[i];
+    }
+}
+template <typename C, int V> __device__ __forceinline__ void xb_load(const C *p, C (&v)[V])
+{
+    if constexpr (std::is_same<C, float>::value && V % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < V / 4; ++i) {
+            const float4 q = reinterpret_cast<const float4 *>(p)[i];
+            v[4 * i] = q.x, v[4 * i + 1] = q.y, v[4 * i + 2] = q.z, v[4 * i + 3] = q.w;
+        }
+    } else if constexpr (std::is_same<C, double>::value && V % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < V / 2; ++i) {
+            const double2 q = reinterpret_cast<const double2 *>(p)[i];
+            v[2 * i] = q.x, v[2 * i + 1] = q.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) v[i] = p[i];
+    }
+}
+
 template <int SHAPE, int R> struct NCoeff3 {
     static constexpr int value = SHAPE == SH_STAR ? 6 * R + 1 : (2 * R + 1) * (2 * R + 1) * (2 * R + 1);
 };
@@ -241,11 +278,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
         C *buf = xb + xsel * (TY * TX);
         xsel ^= 1;
 #pragma unroll
-        for (int r = 0; r < RW; ++r) {
-            C *dstp = buf + (warp * RW + r) * TX + lane * V;
-#pragma unroll
-            for (int v = 0; v < V; ++v) dstp[v] = own[r][v];
-        }
+        for (int r = 0; r < RW; ++r) xb_store<C, V>(buf + (warp * RW + r) * TX + lane * V, own[r]);
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < RW + 2 * R; ++q) {
@@ -255,9 +288,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
                 for (int v = 0; v < V; ++v) ext[q][v] = own[q - R][v];
             } else {
                 const int cr = tr < 0 ? 0 : (tr >= TY ? TY - 1 : tr);
-                const C *srcp = buf + cr * TX + lane * V;
-#pragma unroll
-                for (int v = 0; v < V; ++v) ext[q][v] = srcp[v];
+                xb_load<C, V>(buf + cr * TX + lane * V, ext[q]);
             }
         }
     };

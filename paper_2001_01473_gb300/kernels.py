@@ -48,8 +48,11 @@ KERNELS_2D = [
 KERNELS_2D_WIDE = [
     (STAR, 1, range(4, 7), "float", "MODE_PLAIN", "DT_F32", 6, 0),
     (STAR, 2, range(2, 4), "float", "MODE_PLAIN", "DT_F32", 6, 3),
+    (STAR, 3, range(2, 3), "float", "MODE_PLAIN", "DT_F32", 6, 3),
     (BOX, 1, range(3, 6), "float", "MODE_PLAIN", "DT_F32", 6, 3),
 ]
+# (Measured and not kept, no gain over the default width: the radius-4 star
+# and radius-2 box at bT 2, binary16 storage for the radius-1 star and box.)
 # the same for division-type stencils (both forms): (shape, radius, bT
 # range, storage, dtype, cells per lane, CTAs per SM)
 KERNELS_DIV_2D_WIDE = [

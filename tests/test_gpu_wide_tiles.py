@@ -13,7 +13,7 @@ from _gpu_util import assert_bitwise, coeffs_for, gpu_run, oracle_run
 pytestmark = pytest.mark.gpu
 STAR = inputs.STAR
 SH = {"SH_STAR": inputs.STAR, "SH_BOX": inputs.BOX}
-DT = {"DT_F32": "f32", "DT_F64": "f64"}
+DT = {"DT_F32": "f32", "DT_F64": "f64", "DT_F16S": "f16"}
 
 CASES = [(SH[sh], r, DT[dt], 32 * v, bt)
          for sh, r, bts, _s, _m, dt, v, _occ in KERNELS_2D_WIDE for bt in bts]
