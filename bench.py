@@ -433,7 +433,7 @@ def run_ours(args, rank, world, local):
     cfg = plan.config()
     bt = cfg["bT"]
     passes = T // bt + (1 if T % bt else 0)
-    launches_per_step = passes + 1 + (1 if passes > 1 else 0)   # passes + halo copies
+    launches_per_step = plan.launches(T)            # passes (2 launches for a split 3D pass) + halo copies
 
     x = torch.from_numpy(u0).to(dev)
     y = torch.empty_like(x)
@@ -505,7 +505,7 @@ def run_ours(args, rank, world, local):
                                  else "in-run FP64 fma microbenchmark")),
                 "kernel": (f"box1_kernel bT={bt}" if ndim == 3 and shape == BOX and R >= 2
                            else f"sweep{ndim}d_kernel bT={bt} tile_x={cfg['tile_x']}"),
-                "launches_per_step": passes,
+                "passes_per_step": passes,
                 "full_degree_launches": full_passes,
                 "algorithmic_bytes_per_launch": hbm_bytes_launch,
                 "algorithmic_flops_per_launch": flops_launch,

@@ -89,7 +89,10 @@ enum {
  *   tile_y      3D: tile extent along y in cells, overlap included (b_S2); 2D: 1
  *   stream_axis index of the streamed axis in dims[] (0 = slowest)
  *   hsn         streamed cells per stream block (h_SN, Section 3.2)
- *   warps_per_cta, ctas   launch shape of one pass
+ *   warps_per_cta, ctas   launch shape of one pass (ctas of all its launches)
+ *   launches_per_pass     kernel launches of one full-degree pass: 1, or 2
+ *               when a 3D pass runs its ragged last tile column on a narrow
+ *               kernel (32 cells wide, same tile rows)
  *   model_gcells      analytic roofline prediction, GCell-updates/s
  *   measured_gcells   timed throughput of this config during tuning (0 if untimed) */
 typedef struct {
@@ -100,7 +103,7 @@ typedef struct {
     int hsn;
     int warps_per_cta;
     int ctas;
-    int reserved;
+    int launches_per_pass;
     double model_gcells;
     double measured_gcells;
 } an5d_config;
@@ -176,6 +179,12 @@ int an5d_plan_config(const an5d_plan *plan, an5d_config *cfg);
  * If the plan's tile variant does not build bT, the plan returns to the
  * default variant. */
 int an5d_plan_set_config(an5d_plan *plan, int bT, int hsn);
+
+/* Kernel launches that an5d_run enqueues for T steps with the plan's
+ * current configuration: the halo copies plus one launch per pass, two for
+ * a 3D pass that runs its last tile column on the narrow kernel (0 for
+ * T = 0, which is a plain copy).  Negative AN5D_* status on bad input. */
+int64_t an5d_plan_launches(const an5d_plan *plan, int64_t T);
 
 /* Select the sweep kernel's tile variant: 0 = the default width (128 cells
  * along x in 2D), else a tile width along x for which a variant is built

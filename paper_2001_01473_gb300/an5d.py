@@ -61,11 +61,11 @@ class an5d_config(ctypes.Structure):
     _fields_ = [("bT", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("stream_axis", ctypes.c_int), ("hsn", ctypes.c_int),
                 ("warps_per_cta", ctypes.c_int), ("ctas", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("model_gcells", ctypes.c_double),
+                ("launches_per_pass", ctypes.c_int), ("model_gcells", ctypes.c_double),
                 ("measured_gcells", ctypes.c_double)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class an5d_grid_desc(ctypes.Structure):
@@ -125,6 +125,8 @@ def load(path: str = LIB_PATH):
     L.an5d_plan_set_config.restype = I
     L.an5d_plan_set_tile.argtypes = [P, I]
     L.an5d_plan_set_tile.restype = I
+    L.an5d_plan_launches.argtypes = [P, I64]
+    L.an5d_plan_launches.restype = I64
     L.an5d_plan_tune.argtypes = [P, I, I64, P]
     L.an5d_plan_tune.restype = I
     L.an5d_plan_status.argtypes = [P]
@@ -291,6 +293,13 @@ def an5d_plan_set_config(plan: int, bT: int = 0, hsn: int = 0) -> int:
     return _check(load().an5d_plan_set_config(plan, int(bT), int(hsn)))
 
 
+def an5d_plan_launches(plan: int, T: int) -> int:
+    n = load().an5d_plan_launches(plan, int(T))
+    if n < 0:
+        _check(int(n))
+    return int(n)
+
+
 def an5d_plan_set_tile(plan: int, tile_x: int = 0) -> int:
     return _check(load().an5d_plan_set_tile(plan, int(tile_x)))
 
@@ -382,6 +391,10 @@ class Plan:
 
     def set_config(self, bT: int = 0, hsn: int = 0) -> None:
         an5d_plan_set_config(self.handle, bT, hsn)
+
+    def launches(self, T: int) -> int:
+        """Kernel launches one run of T steps enqueues."""
+        return an5d_plan_launches(self.handle, T)
 
     def set_tile(self, tile_x: int = 0) -> None:
         """Select the sweep kernel's tile variant (0 = default width)."""

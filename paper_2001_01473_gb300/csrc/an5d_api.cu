@@ -197,6 +197,11 @@ static int largest_bt(const an5d_plan *p)
 struct PassGeom {
     const KernelEntry *k;
     int tile_stride_x, tiles_x, tile_stride_y, tiles_y, hsn, stream_blocks, units, ctas;
+    // 3D: a narrow kernel for the last tile column when the main tiles leave a
+    // ragged remainder that fits it (tail_k null otherwise): main columns
+    // cover [R, R + tiles_x * tile_stride_x), the narrow one the rest
+    const KernelEntry *tail_k;
+    int tail_stride_x, tail_units;
 };
 
 // Kernel of degree bt in tile variant `tile`, or (tile < 0) in the plan's
@@ -237,9 +242,24 @@ static int pass_geometry(const an5d_plan *p, int bt, int hsn_req, PassGeom *g, i
     const int R = p->radius;
     g->tile_stride_x = g->k->tile_x - 2 * bt * R;
     g->tiles_x = (int)((p->nx + g->tile_stride_x - 1) / g->tile_stride_x);
+    g->tail_k = nullptr;
+    g->tail_stride_x = 0;
+    g->tail_units = 0;
     if (p->ndim == 3) {
         g->tile_stride_y = g->k->tile_y - 2 * bt * R;
         g->tiles_y = (int)((p->ny + g->tile_stride_y - 1) / g->tile_stride_y);
+        // a ragged last column that one narrow tile covers runs on the
+        // narrow kernel (same tile rows) instead of a mostly idle full tile
+        KernelKey tk{p->ndim, p->shape, p->radius, p->dtype, bt, p->post, 0};
+        tk.part = 1;
+        const KernelEntry *t = find_kernel(tk);
+        const int64_t full = p->nx / g->tile_stride_x, rest = p->nx - full * g->tile_stride_x;
+        if (t && t->tile_y == g->k->tile_y && full >= 1 && rest > 0 &&
+            rest <= t->tile_x - 2 * bt * R) {
+            g->tail_k = t;
+            g->tail_stride_x = t->tile_x - 2 * bt * R;
+            g->tiles_x = (int)full;
+        }
     } else {
         g->tile_stride_y = 1;
         g->tiles_y = 1;
@@ -253,6 +273,7 @@ static int pass_geometry(const an5d_plan *p, int bt, int hsn_req, PassGeom *g, i
     if (units > (1ll << 30)) return fail(AN5D_ERR_UNSUPPORTED, "grid too large");
     g->units = (int)units;
     g->ctas = (g->units + g->k->units_per_cta - 1) / g->k->units_per_cta;
+    if (g->tail_k) g->tail_units = g->tiles_y * g->stream_blocks;  // one CTA per tail tile
     return AN5D_OK;
 }
 
@@ -467,8 +488,8 @@ extern "C" int an5d_plan_config(const an5d_plan *p, an5d_config *cfg)
     cfg->stream_axis = 0;
     cfg->hsn = g.hsn;
     cfg->warps_per_cta = g.k->threads / 32;
-    cfg->ctas = g.ctas;
-    cfg->reserved = 0;
+    cfg->ctas = g.ctas + g.tail_units;
+    cfg->launches_per_pass = g.tail_k ? 2 : 1;
     cfg->model_gcells = p->model_gcells;
     cfg->measured_gcells = p->measured_gcells;
     return ok();
@@ -487,6 +508,28 @@ extern "C" int an5d_plan_set_config(an5d_plan *p, int bt, int hsn)
     p->model_gcells = model_for(p, p->bt, p->hsn);
     p->measured_gcells = 0.0;
     return ok();
+}
+
+extern "C" int64_t an5d_plan_launches(const an5d_plan *p, int64_t T)
+{
+    if (!p) return fail(AN5D_ERR_INVALID_ARG, "NULL plan");
+    if (T < 0) return fail(AN5D_ERR_INVALID_ARG, "T must be >= 0");
+    if (T == 0) return 0;  // one device-to-device copy, no kernel
+    const int64_t full = T / p->bt;
+    const int rem = (int)(T % p->bt);
+    const int64_t np = full + (rem ? 1 : 0);
+    int64_t n = np > 1 ? 2 : 1;  // halo copies into out (and into the scratch grid)
+    PassGeom g;
+    if (full) {
+        if (int s = pass_geometry(p, p->bt, p->hsn, &g)) return s;
+        n += full * (g.tail_k ? 2 : 1);
+    }
+    if (rem) {
+        if (int s = pass_geometry(p, rem, p->hsn, &g)) return s;
+        n += g.tail_k ? 2 : 1;
+    }
+    ok();
+    return n;
 }
 
 extern "C" int an5d_plan_set_tile(an5d_plan *p, int tile_x)
@@ -546,6 +589,7 @@ static int launch_pass(const an5d_plan *p, int bt, const void *src, void *dst, c
     d.ny = (int)p->ny;
     d.nx = (int)p->nx;
     d.tile_stride_x = g.tile_stride_x;
+    d.x_base = p->radius;
     d.tile_stride_y = g.tile_stride_y;
     d.tiles_x = g.tiles_x;
     d.tiles_y = g.tiles_y;
@@ -557,6 +601,17 @@ static int launch_pass(const an5d_plan *p, int bt, const void *src, void *dst, c
     d.post_c = p->post_c;
     for (int k = 0; k < p->n; ++k) d.coeffs[k] = p->coeffs[k];
     CUDA_TRY(g.k->launch(d, st));
+    if (g.tail_k) {
+        // the last tile column, on the narrow kernel: its own row box, its
+        // tiles start where the main columns' compute regions end
+        if (int s = encode_row_map(&d.tmap, src, p->dtype, p->total, g.tail_k->tile_x + A)) return s;
+        d.tile_stride_x = g.tail_stride_x;
+        d.x_base = p->radius + g.tiles_x * g.tile_stride_x;
+        d.tiles_x = 1;
+        d.total_units = g.tail_units;
+        d.ctas = g.tail_units;
+        CUDA_TRY(g.tail_k->launch(d, st));
+    }
     return AN5D_OK;
 }
 
@@ -911,6 +966,7 @@ int plan_fill_pass(const an5d_plan *p, int bt, int tile, const void *src, void *
     d->ny = (int)p->ny;
     d->nx = (int)p->nx;
     d->tile_stride_x = g.tile_stride_x;
+    d->x_base = p->radius;
     d->tile_stride_y = g.tile_stride_y;
     d->tiles_x = g.tiles_x;
     d->tiles_y = g.tiles_y;

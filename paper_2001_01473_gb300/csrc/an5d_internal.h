@@ -33,6 +33,7 @@ struct PassDesc {
     int64_t plane;           // elements per padded xy plane (3D)
     int nz, ny, nx;          // interior extents (nz = 1 in 2D)
     int tile_stride_x;       // output columns per tile along x
+    int x_base;              // 3D: padded column where tile column 0's compute region starts
     int tile_stride_y;       // 3D: output rows per tile along y
     int tiles_x, tiles_y;    // tiles per axis
     int hsn;                 // output rows (2D) / planes (3D) per stream block
@@ -50,10 +51,11 @@ struct KernelKey {
     int ndim, shape, radius, dtype, bt;
     int post = POST_NONE;
     int tile = 0;  // tile variant: 0 = the default kernel, else its tile width along x
+    int part = 0;  // 0 = a pass's kernel; 1 = the narrow kernel of a 3D pass's last tile column
     bool operator==(const KernelKey &o) const
     {
         return ndim == o.ndim && shape == o.shape && radius == o.radius && dtype == o.dtype &&
-               bt == o.bt && post == o.post && tile == o.tile;
+               bt == o.bt && post == o.post && tile == o.tile && part == o.part;
     }
 };
 

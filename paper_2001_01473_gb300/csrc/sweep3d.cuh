@@ -82,6 +82,7 @@ template <typename S, int N> struct Sweep3DArgs {
     int py;           // padded rows per plane ny + 2R
     int nz, ny, nx;   // interior extents
     int tsx, tsy;     // output columns / rows per tile
+    int xb0;          // padded column where tile column 0's compute region starts
     int tiles_x, tiles_y;
     int hsn;          // output planes per stream block
     int total_ctas;   // tiles_x * tiles_y * stream blocks
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
     const int xt = cta % a.tiles_x;
     const int yt = (cta / a.tiles_x) % a.tiles_y;
     const int zb = cta / (a.tiles_x * a.tiles_y);
-    const int x0 = R - BT * R + xt * a.tsx;   // padded column of the tile's first cell
+    const int x0 = a.xb0 - BT * R + xt * a.tsx;   // padded column of the tile's first cell
     const int yb = R - BT * R + yt * a.tsy;   // padded row of the tile's first row
     const int px = a.px, py = a.py, nz = a.nz, ny = a.ny, nx = a.nx;
     const int nplanes = nz + 2 * R;
@@ -547,6 +548,7 @@ cudaError_t launch_sweep3d(const PassDesc &d, cudaStream_t st)
     a.nx = d.nx;
     a.tsx = d.tile_stride_x;
     a.tsy = d.tile_stride_y;
+    a.xb0 = d.x_base;
     a.tiles_x = d.tiles_x;
     a.tiles_y = d.tiles_y;
     a.hsn = d.hsn;
@@ -563,13 +565,16 @@ cudaError_t launch_sweep3d(const PassDesc &d, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// PART_ = 1 registers the kernel as the narrow last-column kernel of the
+// passes whose main kernel has the same key (same NW and RW: same tile rows).
 template <int SHAPE, int R, int BT, typename S, int MODE, int NW, int POST = POST_NONE,
-          int V_ = CELLS_PER_LANE, int RW_ = 2>
+          int V_ = CELLS_PER_LANE, int RW_ = 2, int PART_ = 0>
 KernelEntry entry3d(int dtype)
 {
     using G = Sweep3DGeom<S, SHAPE, BT, R, NW, V_, RW_>;
     KernelEntry e;
     e.key = KernelKey{3, SHAPE, R, dtype, BT, POST};
+    e.key.part = PART_;
     e.launch = &launch_sweep3d<SHAPE, R, BT, S, MODE, NW, POST, V_, RW_>;
     e.func = reinterpret_cast<const void *>(&sweep3d_kernel<SHAPE, R, BT, S, MODE, NW, POST, V_, RW_>);
     e.threads = NW * 32;

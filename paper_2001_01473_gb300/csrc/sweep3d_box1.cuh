@@ -241,6 +241,7 @@ cudaError_t launch_box1(const PassDesc &d, cudaStream_t st)
     a.nx = d.nx;
     a.tsx = d.tile_stride_x;
     a.tsy = d.tile_stride_y;
+    a.xb0 = d.x_base;  // unused: one-level tiles start at column 0
     a.tiles_x = d.tiles_x;
     a.tiles_y = d.tiles_y;
     a.hsn = d.hsn;

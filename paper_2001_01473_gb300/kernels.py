@@ -92,6 +92,15 @@ def geom3d(shape, r, s):
     return (2, 4) if (s == "double" and shape == STAR and r == 1) else (4, 2)
 
 
+# 3D kernels that also get a narrow (one cell per lane, 32-cell-wide) kernel
+# for a pass's ragged last tile column: with 128-cell tiles a 512-wide grid
+# is 4 x (128 - 2 bT R) columns plus a remainder of a few dozen, which would
+# otherwise take a fifth, mostly idle, full tile.  Radius 1 only (a lane's
+# x neighbours must sit in the adjacent lanes); FP32 plain and division.
+def tail3d(shape, r, s, mode):
+    return r == 1 and s == "float" and mode == "MODE_PLAIN"
+
+
 # One-level 3D box sweeps for radius 2-4 (sweep3d_box1.cuh): (radius, storage
 # type, dtype tag, warps per CTA, rows per warp).  Each runs at bT = 1.
 KERNELS_3D_BOX1 = [
@@ -136,6 +145,8 @@ def instantiations():
         v, rw = geom3d(shape, r, s)
         for bt in bts:
             yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, {mode}, {nw}, POST_NONE, {v}, {rw}>({dt})"
+            if tail3d(shape, r, s, mode):
+                yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, {mode}, {nw}, POST_NONE, 1, {rw}, 1>({dt})"
     for r, s, dt, nw, rw in KERNELS_3D_BOX1:
         yield "sweep3d_box1.cuh", f"entry_box1<{r}, {s}, {nw}, {rw}>({dt})"
     for post in POSTS:
@@ -149,3 +160,6 @@ def instantiations():
             v, rw = geom3d(shape, r, s)
             for bt in bts:
                 yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {nw}, {post}, {v}, {rw}>({dt})"
+                if tail3d(shape, r, s, "MODE_PLAIN"):
+                    yield "sweep3d.cuh", (f"entry3d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {nw}, {post}, 1, {rw}, 1>"
+                                          f"({dt})")

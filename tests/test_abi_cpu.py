@@ -78,6 +78,7 @@ def test_null_plan_calls_fail_cleanly(lib):
     assert lib.an5d_plan_status(None) == an5d.AN5D_ERR_INVALID_ARG
     assert lib.an5d_plan_set_config(None, 1, 0) == an5d.AN5D_ERR_INVALID_ARG
     assert lib.an5d_plan_set_tile(None, 0) == an5d.AN5D_ERR_INVALID_ARG
+    assert lib.an5d_plan_launches(None, 5) == an5d.AN5D_ERR_INVALID_ARG
     lib.an5d_plan_destroy(None)   # NULL-safe
     assert an5d.an5d_version().startswith("an5d")
 

@@ -120,3 +120,30 @@ def test_full_size_3d_heat_precision_forms_sampled(dt):
         want = _window_reference_3d(STAR, 1, c, dt, u0, T, p)
         got = y[p].item()
         assert got == float(want), (p, got, want)
+
+
+@pytest.mark.parametrize("shape,bt", [(STAR, 3), (STAR, 1), (BOX, 3), (STAR, 4)])
+@pytest.mark.parametrize("rest", ["narrow", "narrow+1", "one", "none"])
+def test_narrow_last_column(shape, bt, rest):
+    """A ragged remainder of at most one narrow tile's compute width runs on
+    the 32-cell kernel (two launches per pass); one cell wider, or none at
+    all, stays on full tiles.  Bit-exact either way."""
+    R = 1
+    tsx, ts_narrow = 128 - 2 * bt * R, 32 - 2 * bt * R
+    # two full columns plus the remainder
+    rest = {"narrow": ts_narrow, "narrow+1": ts_narrow + 1, "one": 1, "none": 0}[rest]
+    nx = 2 * tsx + rest
+    dims = (9, 30, nx)
+    c = coeffs_for(3, shape, R, seed=3)
+    u0 = inputs.field(dims, R, 2, "f32")
+    T = 2 * bt + 1
+    with an5d.Plan(3, shape, R, c, "f32", dims) as plan:
+        plan.set_config(bt, 4)
+        cfg = plan.config()
+        assert cfg["launches_per_pass"] == (2 if 0 < rest <= ts_narrow else 1), (cfg, rest)
+        # 2 halo copies + 3 passes (2 of bT, 1 of 1 step), a narrow launch more where split
+        n = plan.launches(T)
+        assert 5 + 2 * (cfg["launches_per_pass"] - 1) <= n <= 8, n
+        got = gpu_run(3, shape, R, c, "f32", dims, u0, T, plan=plan)
+    ref = oracle_run(3, shape, R, c, "f32", dims, u0, T)
+    assert_bitwise(got, ref, f"nx={nx} bT={bt}")
