@@ -95,10 +95,11 @@ def geom3d(shape, r, s):
 # 3D kernels that also get a narrow (one cell per lane, 32-cell-wide) kernel
 # for a pass's ragged last tile column: with 128-cell tiles a 512-wide grid
 # is 4 x (128 - 2 bT R) columns plus a remainder of a few dozen, which would
-# otherwise take a fifth, mostly idle, full tile.  Radius 1 only (a lane's
-# x neighbours must sit in the adjacent lanes); FP32 plain and division.
+# otherwise take a fifth, mostly idle, full tile (FP64 star: 64-cell tiles,
+# 8 columns plus a remainder).  Radius 1 only: a lane's x neighbours must
+# sit in the adjacent lanes.
 def tail3d(shape, r, s, mode):
-    return r == 1 and s == "float" and mode == "MODE_PLAIN"
+    return r == 1
 
 
 # One-level 3D box sweeps for radius 2-4 (sweep3d_box1.cuh): (radius, storage
