@@ -92,14 +92,18 @@ def geom3d(shape, r, s):
     return (2, 4) if (s == "double" and shape == STAR and r == 1) else (4, 2)
 
 
-# 3D kernels that also get a narrow (one cell per lane, 32-cell-wide) kernel
-# for a pass's ragged last tile column: with 128-cell tiles a 512-wide grid
-# is 4 x (128 - 2 bT R) columns plus a remainder of a few dozen, which would
-# otherwise take a fifth, mostly idle, full tile (FP64 star: 64-cell tiles,
-# 8 columns plus a remainder).  Radius 1 only: a lane's x neighbours must
-# sit in the adjacent lanes.
+# Cells per lane of the narrow kernel that a 3D kernel gets for a pass's
+# ragged last tile column (0: none).  With 128-cell tiles a 512-wide grid is
+# 4 x (128 - 2 bT R) columns plus a remainder of a few dozen, which would
+# otherwise take a fifth, mostly idle, full tile (FP64 radius-1 star:
+# 64-cell tiles, 8 columns plus a remainder).  A lane's x neighbours must
+# sit in the adjacent lanes, so the narrow kernel has R cells per lane:
+# 32 or 64 cells wide for radius 1 or 2.  (A 96-cell kernel for radius 3
+# measured slower than the full fifth tile: the narrow launch runs after the
+# main one, and at 3 cells per lane it saves too little to pay for its own
+# partial wave; radius 4 would need the full width.)
 def tail3d(shape, r, s, mode):
-    return r == 1
+    return r if r <= 2 and shape == STAR or r == 1 else 0
 
 
 # One-level 3D box sweeps for radius 2-4 (sweep3d_box1.cuh): (radius, storage
@@ -146,8 +150,9 @@ def instantiations():
         v, rw = geom3d(shape, r, s)
         for bt in bts:
             yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, {mode}, {nw}, POST_NONE, {v}, {rw}>({dt})"
-            if tail3d(shape, r, s, mode):
-                yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, {mode}, {nw}, POST_NONE, 1, {rw}, 1>({dt})"
+            tv = tail3d(shape, r, s, mode)
+            if tv and tv < v:
+                yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, {mode}, {nw}, POST_NONE, {tv}, {rw}, 1>({dt})"
     for r, s, dt, nw, rw in KERNELS_3D_BOX1:
         yield "sweep3d_box1.cuh", f"entry_box1<{r}, {s}, {nw}, {rw}>({dt})"
     for post in POSTS:
@@ -161,6 +166,7 @@ def instantiations():
             v, rw = geom3d(shape, r, s)
             for bt in bts:
                 yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {nw}, {post}, {v}, {rw}>({dt})"
-                if tail3d(shape, r, s, "MODE_PLAIN"):
-                    yield "sweep3d.cuh", (f"entry3d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {nw}, {post}, 1, {rw}, 1>"
+                tv = tail3d(shape, r, s, "MODE_PLAIN")
+                if tv and tv < v:
+                    yield "sweep3d.cuh", (f"entry3d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {nw}, {post}, {tv}, {rw}, 1>"
                                           f"({dt})")

@@ -122,14 +122,15 @@ def test_full_size_3d_heat_precision_forms_sampled(dt):
         assert got == float(want), (p, got, want)
 
 
-@pytest.mark.parametrize("shape,bt", [(STAR, 3), (STAR, 1), (BOX, 3), (STAR, 4)])
+@pytest.mark.parametrize("shape,R,bt", [(STAR, 1, 3), (STAR, 1, 1), (BOX, 1, 3), (STAR, 1, 4),
+                                        (STAR, 2, 1), (STAR, 2, 2)])
 @pytest.mark.parametrize("rest", ["narrow", "narrow+1", "one", "none"])
-def test_narrow_last_column(shape, bt, rest):
+def test_narrow_last_column(shape, R, bt, rest):
     """A ragged remainder of at most one narrow tile's compute width runs on
-    the 32-cell kernel (two launches per pass); one cell wider, or none at
-    all, stays on full tiles.  Bit-exact either way."""
-    R = 1
-    tsx, ts_narrow = 128 - 2 * bt * R, 32 - 2 * bt * R
+    the narrow kernel (R cells per lane: 32 or 64 cells wide; two launches
+    per pass); one cell wider, or none at all, stays on full tiles.
+    Bit-exact either way."""
+    tsx, ts_narrow = 128 - 2 * bt * R, 32 * R - 2 * bt * R
     # two full columns plus the remainder
     rest = {"narrow": ts_narrow, "narrow+1": ts_narrow + 1, "one": 1, "none": 0}[rest]
     nx = 2 * tsx + rest
@@ -144,6 +145,7 @@ def test_narrow_last_column(shape, bt, rest):
         # 2 halo copies + 3 passes (2 of bT, 1 of 1 step), a narrow launch more where split
         n = plan.launches(T)
         assert 5 + 2 * (cfg["launches_per_pass"] - 1) <= n <= 8, n
+        assert cfg["ctas"] > 0
         got = gpu_run(3, shape, R, c, "f32", dims, u0, T, plan=plan)
     ref = oracle_run(3, shape, R, c, "f32", dims, u0, T)
     assert_bitwise(got, ref, f"nx={nx} bT={bt}")
