@@ -159,6 +159,10 @@ struct an5d_plan {
     int bt = 1;
     int hsn = 0;
     int tile = 0;         // tile variant of the sweep kernel (0 = default width)
+    // 3D: second stream and fork/join events on which a pass's narrow last
+    // column runs beside the main launch (null: the two run one after the other)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double model_gcells = 0, measured_gcells = 0;
     int bt_max = 0;
     int stall_test = 0;  // fault injection (tests only)
@@ -413,11 +417,17 @@ static an5d_plan *plan_create_impl(int ndim, an5d_shape shape, int radius, const
     if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&p->scratch, p->bytes);
+    if (e == cudaSuccess && ndim == 3) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess && ndim == 3) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && ndim == 3) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         fail(e == cudaErrorMemoryAllocation ? AN5D_ERR_OOM : AN5D_ERR_CUDA, "plan setup: %s",
              cudaGetErrorString(e));
         cudaFree(p->d_status);
         cudaFree(p->scratch);
+        if (p->aux) cudaStreamDestroy(p->aux);
+        if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+        if (p->ev_join) cudaEventDestroy(p->ev_join);
         delete p;
         return nullptr;
     }
@@ -473,6 +483,9 @@ extern "C" void an5d_plan_destroy(an5d_plan *p)
     cudaFree(p->stage_in);
     cudaFree(p->stage_out);
     cudaFree(p->work);
+    if (p->aux) cudaStreamDestroy(p->aux);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     if (cur >= 0) cudaSetDevice(cur);
     delete p;
 }
@@ -600,17 +613,33 @@ static int launch_pass(const an5d_plan *p, int bt, const void *src, void *dst, c
     d.stall_test = p->ndim == 2 ? p->stall_test : 0;
     d.post_c = p->post_c;
     for (int k = 0; k < p->n; ++k) d.coeffs[k] = p->coeffs[k];
-    CUDA_TRY(g.k->launch(d, st));
-    if (g.tail_k) {
-        // the last tile column, on the narrow kernel: its own row box, its
-        // tiles start where the main columns' compute regions end
-        if (int s = encode_row_map(&d.tmap, src, p->dtype, p->total, g.tail_k->tile_x + A)) return s;
-        d.tile_stride_x = g.tail_stride_x;
-        d.x_base = p->radius + g.tiles_x * g.tile_stride_x;
-        d.tiles_x = 1;
-        d.total_units = g.tail_units;
-        d.ctas = g.tail_units;
-        CUDA_TRY(g.tail_k->launch(d, st));
+    if (!g.tail_k) {
+        CUDA_TRY(g.k->launch(d, st));
+        return AN5D_OK;
+    }
+    // the last tile column, on the narrow kernel: its own row box, its tiles
+    // start where the main columns' compute regions end.  It writes cells
+    // the main launch does not touch, so with the plan's second stream it
+    // runs beside the main launch (forked after, and joined before, whatever
+    // `st` holds around this pass) and its CTAs fill the main launch's last
+    // wave instead of waiting for it.
+    PassDesc dt = d;
+    if (int s = encode_row_map(&dt.tmap, src, p->dtype, p->total, g.tail_k->tile_x + A)) return s;
+    dt.tile_stride_x = g.tail_stride_x;
+    dt.x_base = p->radius + g.tiles_x * g.tile_stride_x;
+    dt.tiles_x = 1;
+    dt.total_units = g.tail_units;
+    dt.ctas = g.tail_units;
+    if (p->aux) {
+        CUDA_TRY(cudaEventRecord(p->ev_fork, st));
+        CUDA_TRY(cudaStreamWaitEvent(p->aux, p->ev_fork, 0));
+        CUDA_TRY(g.tail_k->launch(dt, p->aux));
+        CUDA_TRY(cudaEventRecord(p->ev_join, p->aux));
+        CUDA_TRY(g.k->launch(d, st));
+        CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
+    } else {
+        CUDA_TRY(g.k->launch(d, st));
+        CUDA_TRY(g.tail_k->launch(dt, st));
     }
     return AN5D_OK;
 }

@@ -149,3 +149,43 @@ def test_narrow_last_column(shape, R, bt, rest):
         got = gpu_run(3, shape, R, c, "f32", dims, u0, T, plan=plan)
     ref = oracle_run(3, shape, R, c, "f32", dims, u0, T)
     assert_bitwise(got, ref, f"nx={nx} bT={bt}")
+
+
+def test_narrow_column_runs_in_a_captured_graph():
+    """A split pass forks its narrow launch onto the plan's second stream and
+    joins it back; captured into a CUDA graph (torch's capture on the
+    caller's stream) and replayed on new contents of the captured input, it
+    still gives the oracle's bits, and a run on the legacy default stream
+    does too."""
+    import torch
+    R, bt = 1, 3
+    dims = (11, 28, 2 * (128 - 2 * bt * R) + 20)
+    c = coeffs_for(3, STAR, R, seed=6)
+    T = 2 * bt + 2
+    with an5d.Plan(3, STAR, R, c, "f32", dims) as plan:
+        plan.set_config(bt, 5)
+        assert plan.config()["launches_per_pass"] == 2
+        x = torch.empty(inputs.padded_shape(dims, R), dtype=torch.float32, device="cuda")
+        y = torch.empty_like(x)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            x.copy_(torch.from_numpy(inputs.field(dims, R, 1, "f32")))
+            plan.run(x, y, T)                       # warm-up outside the capture
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            plan.run(x, y, T)
+        for seed in (2, 3):
+            u0 = inputs.field(dims, R, seed, "f32")
+            x.copy_(torch.from_numpy(u0))
+            g.replay()
+            torch.cuda.synchronize()
+            assert plan.status() == 0
+            assert_bitwise(y.cpu().numpy(), oracle_run(3, STAR, R, c, "f32", dims, u0, T), f"replay {seed}")
+        u0 = inputs.field(dims, R, 4, "f32")
+        x.copy_(torch.from_numpy(u0))
+        torch.cuda.synchronize()
+        plan.run(x, y, T, stream=0)                 # legacy default stream
+        torch.cuda.synchronize()
+        assert_bitwise(y.cpu().numpy(), oracle_run(3, STAR, R, c, "f32", dims, u0, T), "default stream")
