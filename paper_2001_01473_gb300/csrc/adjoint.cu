@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<float, S
     tg.pitch = a.pitch;
     tg.ny = a.ny;
     tg.nx = a.nx;
-    tg.x0 = R - BT * R + xt * a.tile_stride;
+    tg.x0 = a.xb0 - BT * R + xt * a.tile_stride;
     tg.sc0 = max(R, tg.x0 + BT * R);
     tg.sc1 = min(a.nx + R, tg.x0 + BT * R + a.tile_stride);
     tg.y0 = R + sbk * a.hsn;
@@ -245,6 +245,7 @@ cudaError_t launch_levels(const PassDesc &d, const LevelPtrs &lv, cudaStream_t s
     a.ny = d.ny;
     a.nx = d.nx;
     a.tile_stride = d.tile_stride_x;
+    a.xb0 = d.x_base;
     a.tiles_x = d.tiles_x;
     a.hsn = d.hsn;
     a.total_warps = d.total_units;

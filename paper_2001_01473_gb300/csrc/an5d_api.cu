@@ -201,6 +201,11 @@ static int largest_bt(const an5d_plan *p)
 struct PassGeom {
     const KernelEntry *k;
     int tile_stride_x, tiles_x, tile_stride_y, tiles_y, hsn, stream_blocks, units, ctas;
+    // padded column where tile column 0's compute region starts: R in 3D; in
+    // 2D R rounded down to even, so that tiles start on even columns (the 2D
+    // sweep moves 8-byte pairs when rows and tiles are even; the halo column
+    // a radius-1 first tile takes in is never stored)
+    int x_base;
     // 3D: a narrow kernel for the last tile column when the main tiles leave a
     // ragged remainder that fits it (tail_k null otherwise): main columns
     // cover [R, R + tiles_x * tile_stride_x), the narrow one the rest
@@ -245,7 +250,8 @@ static int pass_geometry(const an5d_plan *p, int bt, int hsn_req, PassGeom *g, i
                     p->ndim, p->shape, p->radius, p->dtype, bt);
     const int R = p->radius;
     g->tile_stride_x = g->k->tile_x - 2 * bt * R;
-    g->tiles_x = (int)((p->nx + g->tile_stride_x - 1) / g->tile_stride_x);
+    g->x_base = p->ndim == 2 ? (R & ~1) : R;
+    g->tiles_x = (int)((p->nx + R - g->x_base + g->tile_stride_x - 1) / g->tile_stride_x);
     g->tail_k = nullptr;
     g->tail_stride_x = 0;
     g->tail_units = 0;
@@ -602,7 +608,7 @@ static int launch_pass(const an5d_plan *p, int bt, const void *src, void *dst, c
     d.ny = (int)p->ny;
     d.nx = (int)p->nx;
     d.tile_stride_x = g.tile_stride_x;
-    d.x_base = p->radius;
+    d.x_base = g.x_base;
     d.tile_stride_y = g.tile_stride_y;
     d.tiles_x = g.tiles_x;
     d.tiles_y = g.tiles_y;
@@ -995,7 +1001,7 @@ int plan_fill_pass(const an5d_plan *p, int bt, int tile, const void *src, void *
     d->ny = (int)p->ny;
     d->nx = (int)p->nx;
     d->tile_stride_x = g.tile_stride_x;
-    d->x_base = p->radius;
+    d->x_base = g.x_base;
     d->tile_stride_y = g.tile_stride_y;
     d->tiles_x = g.tiles_x;
     d->tiles_y = g.tiles_y;

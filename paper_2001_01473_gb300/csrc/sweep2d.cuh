@@ -50,6 +50,7 @@ template <typename S, int N> struct Sweep2DArgs {
     int pitch;        // padded row length nx + 2R (elements)
     int ny, nx;       // interior extents
     int tile_stride;  // output columns per tile: 32*V - 2*bT*R
+    int xb0;          // padded column where tile 0's compute region starts
     int tiles_x;
     int hsn;          // output rows per stream block
     int total_warps;  // tiles_x * stream blocks
@@ -59,6 +60,15 @@ template <typename S, int N> struct Sweep2DArgs {
     typename StorageTraits<S>::C post_c;   // divisor or reciprocal (division-type stencils)
     unsigned long long post_p;             // FP32: (post_c, post_c)
 };
+
+// One 8-byte pair of FP32 cells to global memory, stored if bit `bit` of
+// `mask` is set.
+__device__ __forceinline__ void st_pair_pred(float *p, float a, float b, unsigned mask, int bit)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q st.global.v2.f32 [%0], {%1, %2};\n\t}" ::"l"(p),
+                 "f"(a), "f"(b), "r"(mask & (1u << bit))
+                 : "memory");
+}
 
 template <typename S, int BT, int R, int V_ = CELLS_PER_LANE> struct Sweep2DGeom {
     static constexpr int V = V_;  // consecutive x cells per lane
@@ -222,6 +232,43 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
 #pragma unroll
         for (int v = 0; v < V; ++v) st_pred<S>(out + v, to_storage<S>(res[v]), store_bits, v);
     };
+    // 8-byte pairs: with an even tile origin and an even pitch every row's
+    // cells of a lane start on an 8-byte boundary, in the staging ring and in
+    // the destination.  If no lane stores just one cell of a pair (interior
+    // tiles at an even bT*R), the interior groups read and store pairs.
+    constexpr bool PAIRABLE = std::is_same<S, float>::value && V % 2 == 0 && !RAW && !LEVELS;
+    unsigned pair_bits = 0;  // bit h: cells 2h and 2h+1 are stored
+    bool paired = false;
+    if constexpr (PAIRABLE) {
+        bool partial = false;
+#pragma unroll
+        for (int h = 0; h < V / 2; ++h) {
+            const unsigned two = (store_bits >> (2 * h)) & 3u;
+            if (two == 3u) pair_bits |= 1u << h;
+            partial |= (two == 1u || two == 2u);
+        }
+        paired = __all_sync(FULL_MASK, !partial) && (x0 & 1) == 0 && (pitch & 1) == 0;
+    }
+    auto store_row_pairs = [&](int j, const C (&res)[V]) {
+        if constexpr (PAIRABLE) {
+            float *out = dst + (j * pitch + col0);
+#pragma unroll
+            for (int h = 0; h < V / 2; ++h) st_pair_pred(out + 2 * h, res[2 * h], res[2 * h + 1], pair_bits, h);
+        }
+    };
+    // Level-0 row i (ring slot sb+k) -> registers, as pairs (paired rows only).
+    auto load_row_pairs = [&](int i, int k, C (&row)[V]) -> bool {
+        if constexpr (PAIRABLE) {
+            if (!mbar_wait_warp(&bars[sb + k], par, status)) return false;
+            const float2 *src = reinterpret_cast<const float2 *>(row_in_slot(i, sb + k));
+#pragma unroll
+            for (int h = 0; h < V / 2; ++h) {
+                const float2 q = src[h];
+                row[2 * h] = q.x, row[2 * h + 1] = q.y;
+            }
+        }
+        return true;
+    };
     // Level-0 row i (ring slot sb+k) -> registers.  Returns false on a timeout.
     auto load_row = [&](int i, int k, bool have, C (&row)[V]) -> bool {
         if (have) {
@@ -284,9 +331,10 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
 #pragma unroll
                 for (int h = 0; h < H; ++h) rr[t][s2][h] = 0ull;
 
-        auto group = [&](auto check_tag, auto edge_tag, int ib) -> bool {
+        auto group = [&](auto check_tag, auto edge_tag, auto pair_tag, int ib) -> bool {
             constexpr bool CHECK = decltype(check_tag)::value;
             constexpr bool EDGE = decltype(edge_tag)::value;
+            constexpr bool PAIR = decltype(pair_tag)::value;
             prefetch_group(ib);
 #pragma unroll
             for (int k = 0; k < P; ++k) {
@@ -294,7 +342,8 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
                 if (CHECK && i >= iend) return true;
                 {
                     float row[V];
-                    if (!load_row(i, k, !CHECK || i < nrows, row)) return false;
+                    if (PAIR ? !load_row_pairs(i, k, row) : !load_row(i, k, !CHECK || i < nrows, row))
+                        return false;
 #pragma unroll
                     for (int h = 0; h < H; ++h) rr[0][k][h] = f2_pack(row[2 * h], row[2 * h + 1]);
                 }
@@ -369,7 +418,10 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
                         float res[V];
 #pragma unroll
                         for (int h = 0; h < H; ++h) f2_unpack(acc[h], res[2 * h], res[2 * h + 1]);
-                        store_row(j, res);
+                        if (PAIR)
+                            store_row_pairs(j, res);
+                        else
+                            store_row(j, res);
                     }
                 }
             }
@@ -380,11 +432,14 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
             const bool fast = (ib - BT * R >= y0) && (ib + P - 1 - BT * R < y1) &&
                               (ib - BT * R >= R) && (ib + P - 1 - R < ny + R);
             bool ok;
-            if (fast)
-                ok = edge ? group(std::false_type{}, std::true_type{}, ib)
-                          : group(std::false_type{}, std::false_type{}, ib);
+            if (fast && edge)
+                ok = group(std::false_type{}, std::true_type{}, std::false_type{}, ib);
+            else if (fast && paired)
+                ok = group(std::false_type{}, std::false_type{}, std::true_type{}, ib);
+            else if (fast)
+                ok = group(std::false_type{}, std::false_type{}, std::false_type{}, ib);
             else
-                ok = group(std::true_type{}, std::true_type{}, ib);
+                ok = group(std::true_type{}, std::true_type{}, std::false_type{}, ib);
             if (!ok) {
                 drain(ib);
                 return false;
@@ -401,16 +456,18 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
 #pragma unroll
                 for (int h = 0; h < H; ++h) pa[t][s2][h] = 0ull;
 
-        auto group = [&](auto check_tag, auto edge_tag, int ib) -> bool {
+        auto group = [&](auto check_tag, auto edge_tag, auto pair_tag, int ib) -> bool {
             constexpr bool CHECK = decltype(check_tag)::value;
             constexpr bool EDGE = decltype(edge_tag)::value;
+            constexpr bool PAIR = decltype(pair_tag)::value;
             prefetch_group(ib);
 #pragma unroll
             for (int k = 0; k < P; ++k) {
                 const int i = ib + k;
                 if (CHECK && i >= iend) return true;
                 float in_row[V];
-                if (!load_row(i, k, !CHECK || i < nrows, in_row)) return false;
+                if (PAIR ? !load_row_pairs(i, k, in_row) : !load_row(i, k, !CHECK || i < nrows, in_row))
+                    return false;
 #pragma unroll
                 for (int t = 1; t <= BT; ++t) {
                     const int ar = i - (t - 1) * R;
@@ -487,7 +544,10 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
 #pragma unroll
                         for (int v = 0; v < V; ++v) in_row[v] = out_row[v];
                     } else if (!CHECK || (e_row >= y0 && e_row < y1)) {
-                        store_row(e_row, out_row);
+                        if (PAIR)
+                            store_row_pairs(e_row, out_row);
+                        else
+                            store_row(e_row, out_row);
                     }
                 }
             }
@@ -498,11 +558,14 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
             const bool fast = (ib - BT * R >= y0) && (ib + P - 1 - BT * R < y1) &&
                               (ib - BT * R >= R) && (ib + P - 1 + R < ny + R);
             bool ok;
-            if (fast)
-                ok = edge ? group(std::false_type{}, std::true_type{}, ib)
-                          : group(std::false_type{}, std::false_type{}, ib);
+            if (fast && edge)
+                ok = group(std::false_type{}, std::true_type{}, std::false_type{}, ib);
+            else if (fast && paired)
+                ok = group(std::false_type{}, std::false_type{}, std::true_type{}, ib);
+            else if (fast)
+                ok = group(std::false_type{}, std::false_type{}, std::false_type{}, ib);
             else
-                ok = group(std::true_type{}, std::true_type{}, ib);
+                ok = group(std::true_type{}, std::true_type{}, std::false_type{}, ib);
             if (!ok) {
                 drain(ib);
                 return false;
@@ -720,7 +783,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32,
     tg.pitch = a.pitch;
     tg.ny = a.ny;
     tg.nx = a.nx;
-    tg.x0 = R - BT * R + xt * a.tile_stride;
+    tg.x0 = a.xb0 - BT * R + xt * a.tile_stride;
     tg.sc0 = max(R, tg.x0 + BT * R);
     tg.sc1 = min(a.nx + R, tg.x0 + BT * R + a.tile_stride);
     tg.y0 = R + sbk * a.hsn;
@@ -749,6 +812,7 @@ cudaError_t launch_sweep2d(const PassDesc &d, cudaStream_t st)
     a.ny = d.ny;
     a.nx = d.nx;
     a.tile_stride = d.tile_stride_x;
+    a.xb0 = d.x_base;
     a.tiles_x = d.tiles_x;
     a.hsn = d.hsn;
     a.total_warps = d.total_units;
