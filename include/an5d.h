@@ -92,7 +92,7 @@ enum {
  *   warps_per_cta, ctas   launch shape of one pass (ctas of all its launches)
  *   launches_per_pass     kernel launches of one full-degree pass: 1, or 2
  *               when a 3D pass runs its ragged last tile column on a narrow
- *               kernel (32 cells wide, same tile rows)
+ *               kernel (32 or 64 cells wide, same tile rows)
  *   model_gcells      analytic roofline prediction, GCell-updates/s
  *   measured_gcells   timed throughput of this config during tuning (0 if untimed) */
 typedef struct {
@@ -123,7 +123,8 @@ int an5d_coeff_count(int ndim, an5d_shape shape, int radius);
  *           the padded array must have fewer than 2^31 elements
  * Picks the blocking with the library's analytic model (no GPU timing; see
  * an5d_plan_tune).  Allocates the plan's scratch buffer (one padded grid)
- * on the current device.  Returns NULL on failure. */
+ * on the current device, and for 3D a second CUDA stream and two events
+ * (see an5d_run); an5d_plan_destroy releases them.  Returns NULL on failure. */
 an5d_plan *an5d_plan_create(int ndim, an5d_shape shape, int radius, const double *coeffs,
                             an5d_dtype dtype, const int64_t *dims);
 
@@ -156,6 +157,10 @@ an5d_plan *an5d_plan_create_div(int ndim, an5d_shape shape, int radius, const do
  *   T        >= 0; T == 0 copies in to out
  *   stream   cudaStream_t as void*
  * Enqueues ceil(T / bT) passes plus a halo copy; returns after enqueueing.
+ * A 3D pass whose last tile column runs on the narrow kernel forks that
+ * launch onto the plan's own second stream after an event recorded on
+ * `stream` and joins it back into `stream` before the next pass, so all of
+ * the run's work is ordered on `stream` (also under stream capture).
  * Not thread-safe per plan: one run of a plan at a time (its scratch
  * buffer is shared by all runs). */
 int an5d_run(an5d_plan *plan, const void *in, void *out, int64_t T, void *stream);
