@@ -202,6 +202,16 @@ int64_t an5d_plan_launches(const an5d_plan *plan, int64_t T);
  * stencil and current bT.  cfg.tile_x reports the width in use. */
 int an5d_plan_set_tile(an5d_plan *plan, int tile_x);
 
+/* Replace the plan's coefficients (n doubles in the canonical offset order,
+ * rounded to the plan's precision as at creation; Section 5.1's constant
+ * coefficients become kernel arguments).  Keeps the stencil, the grid, the
+ * configuration and every buffer the plan owns, so a training loop that
+ * updates the coefficients every step reuses one plan instead of creating
+ * one per step.  Host-side only: the coefficients travel by value in each
+ * launch's arguments, so work already enqueued keeps the coefficients it
+ * was launched with.  AN5D_ERR_INVALID_ARG on a NULL plan or coeffs. */
+int an5d_plan_set_coeffs(an5d_plan *plan, const double *coeffs);
+
 /* Autotune (Section 5.3's "Tuned" procedure with this library's model):
  * rank every built bT and stream-block length of every tile variant with
  * the analytic model, time each variant's top `topk` candidates on the
@@ -239,10 +249,15 @@ int an5d_plan_status(an5d_plan *plan);
  *
  * The first call on a device looks up the array's device address on that
  * device (set-up, once per device); make that first call before any stream
- * capture.  Every call shares the array: calls whose GPU work overlaps (from
- * other host threads or on other streams) race and give wrong results.
- * Synchronous: enqueues on `stream`, waits for it, and returns
- * AN5D_ERR_TIMEOUT if a bounded device wait gave up. */
+ * capture.  A device reset (cudaDeviceReset) after that first call is not
+ * supported, as for plans: the address kept from the first call would no
+ * longer name the array.  Every call shares the array: calls whose GPU work
+ * overlaps (from other host threads or on other streams) race and give wrong
+ * results.  Synchronous: enqueues on `stream`, reads the status word back
+ * and waits for the stream, and returns AN5D_ERR_TIMEOUT if a bounded device
+ * wait gave up.  A call that fails after it has enqueued work still waits
+ * for the stream before it returns, so the array is idle whenever the call
+ * returns. */
 #define AN5D_NOALLOC_MAX_BYTES (32u << 20)
 int an5d_run_noalloc(int ndim, an5d_shape shape, int radius, const double *coeffs,
                      an5d_dtype dtype, const int64_t *dims, const void *in, void *out, int64_t T,

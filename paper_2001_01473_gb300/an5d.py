@@ -125,6 +125,8 @@ def load(path: str = LIB_PATH):
     L.an5d_plan_set_config.restype = I
     L.an5d_plan_set_tile.argtypes = [P, I]
     L.an5d_plan_set_tile.restype = I
+    L.an5d_plan_set_coeffs.argtypes = [P, P]
+    L.an5d_plan_set_coeffs.restype = I
     L.an5d_plan_launches.argtypes = [P, I64]
     L.an5d_plan_launches.restype = I64
     L.an5d_plan_tune.argtypes = [P, I, I64, P]
@@ -304,6 +306,11 @@ def an5d_plan_set_tile(plan: int, tile_x: int = 0) -> int:
     return _check(load().an5d_plan_set_tile(plan, int(tile_x)))
 
 
+def an5d_plan_set_coeffs(plan: int, coeffs) -> int:
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    return _check(load().an5d_plan_set_coeffs(plan, c.ctypes.data))
+
+
 def an5d_plan_tune(plan: int, topk: int = 5, T_probe: int = 20, stream=None) -> int:
     return _check(load().an5d_plan_tune(plan, int(topk), int(T_probe), _stream(stream)))
 
@@ -399,6 +406,10 @@ class Plan:
     def set_tile(self, tile_x: int = 0) -> None:
         """Select the sweep kernel's tile variant (0 = default width)."""
         an5d_plan_set_tile(self.handle, tile_x)
+
+    def set_coeffs(self, coeffs) -> None:
+        """Replace the coefficients; configuration and buffers are kept."""
+        an5d_plan_set_coeffs(self.handle, coeffs)
 
     def tune(self, topk: int = 5, T_probe: int = 20, stream=None) -> dict:
         an5d_plan_tune(self.handle, topk, T_probe, stream)

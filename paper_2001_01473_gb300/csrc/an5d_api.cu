@@ -563,6 +563,14 @@ extern "C" int an5d_plan_set_tile(an5d_plan *p, int tile_x)
     return ok();
 }
 
+extern "C" int an5d_plan_set_coeffs(an5d_plan *p, const double *coeffs)
+{
+    if (!p || !coeffs) return fail(AN5D_ERR_INVALID_ARG, "NULL plan or coeffs");
+    const bool dbl = p->dtype == AN5D_F64;
+    for (int k = 0; k < p->n; ++k) p->coeffs[k] = dbl ? coeffs[k] : (double)(float)coeffs[k];
+    return ok();
+}
+
 static bool overlaps(const void *a, const void *b, size_t n)
 {
     const char *x = (const char *)a, *y = (const char *)b;
@@ -934,26 +942,35 @@ extern "C" int an5d_run_noalloc(int ndim, an5d_shape shape, int radius, const do
     if (int s = check_run_args(&p, in, out, T)) return s;
 
     cudaStream_t st = (cudaStream_t)stream;
-    CUDA_TRY(cudaMemsetAsync(p.d_status, 0, sizeof(int), st));  // the array keeps old contents
-    if (T == 0) {
-        CUDA_TRY(cudaMemcpyAsync(out, in, p.bytes, cudaMemcpyDeviceToDevice, st));
-    } else {
-        // Same pass list as an5d_run, walked without a container.
-        const int64_t full = T / p.bt;
-        const int rem = (int)(T % p.bt);
-        const int64_t np = full + (rem ? 1 : 0);
-        if (int s = launch_halo_copy(&p, in, out, st)) return s;
-        if (np > 1)
-            if (int s = launch_halo_copy(&p, in, p.scratch, st)) return s;
-        const void *src = in;
-        for (int64_t k = 0; k < np; ++k) {
-            void *dst = ((np - 1 - k) % 2 == 0) ? out : p.scratch;
-            if (int s = launch_pass(&p, k < full ? p.bt : rem, src, dst, st)) return s;
-            src = dst;
-        }
-    }
     int h = 0;
-    CUDA_TRY(cudaMemcpyAsync(&h, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    auto enqueue = [&]() -> int {
+        CUDA_TRY(cudaMemsetAsync(p.d_status, 0, sizeof(int), st));  // the array keeps old contents
+        if (T == 0) {
+            CUDA_TRY(cudaMemcpyAsync(out, in, p.bytes, cudaMemcpyDeviceToDevice, st));
+        } else {
+            // Same pass list as an5d_run, walked without a container.
+            const int64_t full = T / p.bt;
+            const int rem = (int)(T % p.bt);
+            const int64_t np = full + (rem ? 1 : 0);
+            if (int s = launch_halo_copy(&p, in, out, st)) return s;
+            if (np > 1)
+                if (int s = launch_halo_copy(&p, in, p.scratch, st)) return s;
+            const void *src = in;
+            for (int64_t k = 0; k < np; ++k) {
+                void *dst = ((np - 1 - k) % 2 == 0) ? out : p.scratch;
+                if (int s = launch_pass(&p, k < full ? p.bt : rem, src, dst, st)) return s;
+                src = dst;
+            }
+        }
+        CUDA_TRY(cudaMemcpyAsync(&h, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        return AN5D_OK;
+    };
+    if (int s = enqueue()) {
+        // work queued before the failure still uses the shared array: let it
+        // finish, so that the array is idle when the call returns
+        cudaStreamSynchronize(st);
+        return s;
+    }
     CUDA_TRY(cudaStreamSynchronize(st));
     if (h & STATUS_TIMEOUT) return fail(AN5D_ERR_TIMEOUT, "a bounded device wait gave up");
     return ok();

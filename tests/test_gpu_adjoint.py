@@ -147,3 +147,79 @@ def test_adjoint_vs_central_differences_gpu():
         trunc = abs((loss_f64(c32 + h * dcv) - loss_f64(c32 - h * dcv)) / (2 * h)
                     - float(np.dot(gc64, dcv)))
         assert abs(fd - an) <= 1.5 * trunc + 1e-3 * abs(an), (fd, an, trunc)
+
+
+@pytest.mark.parametrize("shape,R,dims,T,bt", [(BOX, 2, (2000, 1500), 60, 4),
+                                               (STAR, 1, (3000, 1200), 100, 4),
+                                               (STAR, 2, (1100, 4096), 40, 3)])
+def test_adjoint_at_batch_grid_scale(shape, R, dims, T, bt):
+    """The batched workload's grids reach sides of 4096 and hundreds of steps:
+    the coefficient gradient sums g_{t+1}(p) u_t(p + o_k) over every cell and
+    step (FP32 products, FP64 partial sums), so its error is checked at that
+    scale, against the FP64 oracle adjoint.  Measured relative L2 errors are
+    printed; the bound is the same 1e-4 as on the small grids."""
+    import torch
+    n = inputs.coeff_count(2, shape, R)
+    c = inputs.normalised_coeffs(n, 0)
+    c32 = c.astype(np.float32).astype(np.float64)
+    u0 = inputs.field(dims, R, 1, "f32")
+    tg = inputs.target_field(dims, R, 2, "f32")
+    inner = tuple(slice(R, R + d) for d in dims)
+    with an5d.Plan(2, shape, R, c, "f32", dims) as plan:
+        plan.set_config(bt, 0)
+        x = torch.from_numpy(u0).cuda()
+        y = torch.empty_like(x)
+        plan.run(x, y, T)
+        gT = torch.zeros_like(x)
+        gT[inner] = y[inner] - torch.from_numpy(tg).cuda()[inner]
+        gu = torch.empty_like(x)
+        gc = an5d.an5d_run_adjoint(plan.handle, x, gT, gu, T)[:n]
+        gu = gu.cpu().numpy()
+    _, ref_gu, ref_gc = oracle.adjoint_f64(2, shape, R, c32, dims, u0.astype(np.float64),
+                                           tg.astype(np.float64), T)
+    e_u = _rel(gu[inner].astype(np.float64), ref_gu[inner])
+    e_c = _rel(gc, ref_gc)
+    print(f"adjoint {dims} shape={shape} R={R} T={T}: rel L2 dL/du0 {e_u:.2e}, dL/dc {e_c:.2e}")
+    assert e_u < 1e-4
+    assert e_c < 1e-4, (gc, ref_gc)
+
+
+def test_autograd_training_loop_keeps_one_plan():
+    """A loop that updates the coefficients every step reuses one cached plan
+    (coefficients replaced in place): device memory stays constant over 50
+    backward steps, and the last step's gradients still match the oracle."""
+    import torch
+    from paper_2001_01473_gb300 import autograd
+    dims = (96, 300)
+    shape, R, T = BOX, 1, 7
+    n = inputs.coeff_count(2, shape, R)
+    u0 = inputs.field(dims, R, 1, "f32")
+    tg = torch.from_numpy(inputs.target_field(dims, R, 2, "f32")).cuda()
+    inner = tuple(slice(R, R + d) for d in dims)
+    x = torch.from_numpy(u0).cuda().requires_grad_(True)
+    ct = torch.tensor(inputs.normalised_coeffs(n, 0).astype(np.float32).astype(np.float64),
+                      requires_grad=True)
+    free = []
+    for step in range(50):
+        x.grad = None
+        ct.grad = None
+        uT = autograd.stencil_sweep(x, ct, T, shape, R)
+        loss = 0.5 * ((uT[inner] - tg[inner]) ** 2).double().sum()
+        loss.backward()
+        with torch.no_grad():
+            ct -= 1e-6 * ct.grad      # the coefficients change every step
+            ct.copy_(ct.float().double())
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+    assert sum(1 for k in autograd._plans if k[1:] == (shape, R, dims)) == 1
+    assert max(free[5:]) - min(free[5:]) <= 4 << 20, (min(free[5:]), max(free[5:]))
+    # gradients of the final coefficients
+    x.grad = None
+    ct.grad = None
+    uT = autograd.stencil_sweep(x, ct, T, shape, R)
+    (0.5 * ((uT[inner] - tg[inner]) ** 2).double().sum()).backward()
+    _, ref_gu, ref_gc = oracle.adjoint_f64(2, shape, R, ct.detach().numpy(), dims,
+                                           u0.astype(np.float64),
+                                           tg.cpu().numpy().astype(np.float64), T)
+    assert _rel(x.grad.cpu().numpy()[inner].astype(np.float64), ref_gu[inner]) < 1e-4
+    assert _rel(ct.grad.numpy(), ref_gc) < 1e-4

@@ -20,14 +20,8 @@ for _sh, _r, _bts, _s, _m, _dt in KERNELS_2D:
 
 
 def _cases():
-    out = []
-    for (shape, R, dt), bts in sorted(BUILT.items()):
-        pick = sorted({bts[0], bts[len(bts) // 2], bts[-1]})
-        if (shape, R, dt) in ((STAR, 1, "f32"), (BOX, 1, "f32")):
-            pick = bts
-        for bt in pick:
-            out.append((shape, R, dt, bt))
-    return out
+    # every compiled degree of every (stencil, dtype): the tuner may pick any
+    return [(shape, R, dt, bt) for (shape, R, dt), bts in sorted(BUILT.items()) for bt in bts]
 
 
 @pytest.mark.parametrize("shape,R,dt,bt", _cases())

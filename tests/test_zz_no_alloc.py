@@ -23,6 +23,11 @@ CASES = [
     (2, BOX, 1, "f32c", (70, 260), 9),
     (2, STAR, 3, "f32", (31, 129), 1),     # one pass
     (2, STAR, 1, "f32", (16, 16), 0),      # copy only
+    # 3D: at every degree 1-4 a 136-wide grid is one full 128-cell tile
+    # column plus a remainder that fits the narrow last-column kernel, which
+    # the allocation-free call runs after the main launch on the same stream
+    (3, STAR, 1, "f32", (21, 40, 136), 7),
+    (3, BOX, 1, "f64", (13, 30, 70), 4),   # 3D box, FP64
 ]
 
 
@@ -49,6 +54,10 @@ def test_noalloc_matches_plan_run_two_calls_in_a_row():
     prepared = []
     for i, (ndim, shape, R, dt, dims, T) in enumerate(CASES):
         c = coeffs_for(ndim, shape, R, seed=i)
+        if ndim == 3 and shape == STAR:
+            # both calls pick the same configuration; it splits every pass
+            with an5d.Plan(ndim, shape, R, c, dt, dims) as plan:
+                assert plan.config()["launches_per_pass"] == 2, plan.config()
         u0 = inputs.field(dims, R, 10 + i, dt)
         x = torch.from_numpy(u0).cuda()
         prepared.append((ndim, shape, R, dt, dims, T, c, x,
