@@ -48,6 +48,9 @@ WORKLOADS = {
     "star2d1r-f64": (2, STAR, 1, "f64", (16384, 16384), 1000),
     "star2d2r-f64": (2, STAR, 2, "f64", (16384, 16384), 1000),
     "box2d1r-f64": (2, BOX, 1, "f64", (16384, 16384), 1000),
+    "star2d3r-f64": (2, STAR, 3, "f64", (16384, 16384), 1000),
+    "star2d4r-f64": (2, STAR, 4, "f64", (16384, 16384), 1000),
+    "box2d2r-f64": (2, BOX, 2, "f64", (16384, 16384), 1000),
     "box2d1r-f16": (2, BOX, 1, "f16", (16384, 16384), 1000),
     "box2d1r-f32c": (2, BOX, 1, "f32c", (16384, 16384), 1000),
     "star3d1r-f32": (3, STAR, 1, "f32", (512, 512, 512), 200),
@@ -62,6 +65,12 @@ WORKLOADS = {
     "box3d4r-f32": (3, BOX, 4, "f32", (512, 512, 512), 200),
     "star3d1r-f64": (3, STAR, 1, "f64", (512, 512, 512), 200),
     "box3d1r-f64": (3, BOX, 1, "f64", (512, 512, 512), 200),
+    "star3d2r-f64": (3, STAR, 2, "f64", (512, 512, 512), 200),
+    "star3d3r-f64": (3, STAR, 3, "f64", (512, 512, 512), 200),
+    "star3d4r-f64": (3, STAR, 4, "f64", (512, 512, 512), 200),
+    # the small bit-exact case: 512^2 FP32, T = 64 (1 MB grid, inside L2: the
+    # timed steps flush L2 in between, and the oracle leg checks every cell)
+    "star2d1r-f32-512": (2, STAR, 1, "f32", (512, 512), 64),
     # smaller grids for profiler captures (still larger than the 129 MB L2)
     "star2d1r-f32-8k": (2, STAR, 1, "f32", (8192, 8192), 100),
     "box2d2r-f32-8k": (2, BOX, 2, "f32", (8192, 8192), 100),
@@ -116,6 +125,7 @@ NOMINAL_SMS = 152
 NOMINAL_FP32_LANES = 128
 NOMINAL_MAX_MHZ = 2070.0
 FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20   # written between timed steps of grids that fit in L2 (129 MB)
 
 
 def bytes_per_cell(dtype: str) -> int:
@@ -128,8 +138,65 @@ def flops_per_cell(ndim: int, shape: int, R: int, dtype: str, post=None) -> int:
     compensated form counts Dot2's 10 flops per term."""
     n = inputs.coeff_count(ndim, shape, R)
     if dtype == "f32c":
-        return 10 * n - 8
+        # first term: product + its error by fma (2); each later term: TwoProduct
+        # (2), TwoSum (6), error accumulation (2); the final sum p + s (1)
+        return 10 * n - 7
     return 2 * n - 1 + (1 if post else 0)
+
+
+def built_degrees(ndim, shape, R, dtype, post=None):
+    """Degrees bT compiled for a stencil (any tile variant), from kernels.py."""
+    from paper_2001_01473_gb300 import kernels as K
+    dt = {"f32": "DT_F32", "f64": "DT_F64", "f16": "DT_F16S", "f32c": "DT_F32C"}[dtype]
+    sh = K.STAR if shape == STAR else K.BOX
+    out = set()
+    if post:
+        tabs = [(t[0], t[1], t[2], t[4]) for t in (K.KERNELS_DIV_2D if ndim == 2 else K.KERNELS_DIV_3D)]
+        tabs += [(t[0], t[1], t[2], t[4]) for t in K.KERNELS_DIV_2D_WIDE] if ndim == 2 else []
+    elif ndim == 2:
+        tabs = [(t[0], t[1], t[2], t[5]) for t in K.KERNELS_2D + K.KERNELS_2D_WIDE]
+    else:
+        tabs = [(t[0], t[1], t[2], t[5]) for t in K.KERNELS_3D]
+        tabs += [(K.BOX, t[0], range(1, 2), t[2]) for t in K.KERNELS_3D_BOX1]
+    for s2, r2, bts, d2 in tabs:
+        if s2 == sh and r2 == R and d2 == dt:
+            out.update(bts)
+    return sorted(out)
+
+
+def smem_bytes_per_cell(ndim, shape, R, dtype, bt):
+    """Shared-memory bytes the kernel moves per cell-update, counted from its
+    design (the B_smem of the roofline's shared-memory term):
+      2D sweep: the staged input row, written by TMA and read once per pass:
+        2w / bT;
+      3D sweep: that, plus per level the y exchange: each cell stored once
+        and 2R rows of neighbours read per RW rows a warp owns:
+        wc (1 + 2R / RW), wc the compute word;
+      3D one-level high-order box: the staged plane written once and read
+        over (RW + 2R) rows x (V + 2R) cells per RW x V cells of a thread."""
+    from paper_2001_01473_gb300 import kernels as K
+    w = bytes_per_cell(dtype)
+    wc = 8 if dtype == "f64" else 4
+    if ndim == 2:
+        return 2.0 * w / bt
+    if shape == BOX and R >= 2:
+        rw = {(r, s): rw for r, s, _d, _nw, rw in K.KERNELS_3D_BOX1}[(R, "double" if dtype == "f64" else "float")]
+        v = 4
+        return w * (1.0 + (rw + 2 * R) * (v + 2 * R) / (rw * v))
+    st = {"f64": "double", "f16": "__half"}.get(dtype, "float")
+    _v, rw = K.geom3d(K.STAR if shape == STAR else K.BOX, R, st)
+    return 2.0 * w / bt + wc * (1.0 + 2.0 * R / rw)
+
+
+def roof_terms(ndim, shape, R, dtype, bt, post, hbm_gbs, smem_gbs, alu_tflops):
+    """The three roof terms in cell-updates/s: HBM bytes per bT steps at the
+    copy bandwidth, shared-memory bytes at the shared-memory bandwidth, flops at
+    the FMA peak; the roof is their minimum."""
+    w = bytes_per_cell(dtype)
+    terms = {"hbm": hbm_gbs * 1e9 * bt / (2.0 * w),
+             "smem": smem_gbs * 1e9 / smem_bytes_per_cell(ndim, shape, R, dtype, bt),
+             "alu": alu_tflops * 1e12 / flops_per_cell(ndim, shape, R, dtype, post)}
+    return terms
 
 
 def load_measured_peaks():
@@ -321,9 +388,12 @@ def paper_model_report(an5d, ndim, shape, R, dtype, dims, post, bt, hsn, tile, v
 # ---------------------------------------------------------------------------
 # Reference arm: the CPU oracle.
 
-def oracle_time(ndim, shape, R, dtype, dims, budget_s=12.0, post=None):
+def oracle_time(ndim, shape, R, dtype, dims, budget_s=12.0, post=None, T_full=None, out=None):
     """Time the oracle on a bounded sample of the workload: the full grid for
-    a number of steps chosen so that the run takes about budget_s."""
+    a number of steps chosen so that the run takes about budget_s.  When the
+    workload's whole length T_full fits that budget, exactly T_full steps
+    run; with `out` (the GPU's result of the same workload) the oracle's
+    result is then compared with it bit for bit ("parity" in the result)."""
     import oracle
     c = workload_coeffs(ndim, shape, R, post)
     u0 = inputs.field(dims, R, 1, dtype)
@@ -332,16 +402,15 @@ def oracle_time(ndim, shape, R, dtype, dims, budget_s=12.0, post=None):
     def run(T):
         if post:
             t = np.float64 if dtype == "f64" else np.float32
-            oracle.run_div(dtype, ndim, shape, R, c.astype(t), DIVISOR,
-                           oracle.POST_DIV if post == "div" else oracle.POST_MUL_RCP, dims, u0, T)
-        elif dtype == "f64":
-            oracle.run_f64(ndim, shape, R, c, dims, u0, T)
-        elif dtype == "f16":
-            oracle.run_f16s(ndim, shape, R, c.astype(np.float32), dims, u0, T)
-        elif dtype == "f32c":
-            oracle.run_dot2(ndim, shape, R, c.astype(np.float32), dims, u0, T)
-        else:
-            oracle.run_f32(ndim, shape, R, c.astype(np.float32), dims, u0, T)
+            return oracle.run_div(dtype, ndim, shape, R, c.astype(t), DIVISOR,
+                                  oracle.POST_DIV if post == "div" else oracle.POST_MUL_RCP, dims, u0, T)
+        if dtype == "f64":
+            return oracle.run_f64(ndim, shape, R, c, dims, u0, T)
+        if dtype == "f16":
+            return oracle.run_f16s(ndim, shape, R, c.astype(np.float32), dims, u0, T)
+        if dtype == "f32c":
+            return oracle.run_dot2(ndim, shape, R, c.astype(np.float32), dims, u0, T)
+        return oracle.run_f32(ndim, shape, R, c.astype(np.float32), dims, u0, T)
 
     # per-step cost without the oracle's set-up copies: difference of two runs
     t0 = time.perf_counter()
@@ -352,13 +421,23 @@ def oracle_time(ndim, shape, R, dtype, dims, budget_s=12.0, post=None):
     t3 = time.perf_counter() - t0
     per_step = max((t3 - t1) / 2.0, 1e-4)
     T = max(1, min(1000, int(budget_s / per_step)))
+    whole = T_full is not None and T >= T_full
+    if whole:
+        T = T_full
     t0 = time.perf_counter()
-    run(T)
+    res = run(T)
     dt = time.perf_counter() - t0
-    return {"value": cells * T / dt / 1e9, "unit": "GCell-updates/s", "cores": oracle.get_threads(),
+    line = {"value": cells * T / dt / 1e9, "unit": "GCell-updates/s", "cores": oracle.get_threads(),
             "kind": "oracle", "seconds": round(dt, 3),
-            "sample": f"full {'x'.join(map(str, dims))} grid, T={T} of the workload's steps "
-                      f"(includes the oracle's two buffer copies)"}
+            "sample": (f"full {'x'.join(map(str, dims))} grid, "
+                       + (f"all T={T} steps of the workload" if whole else f"T={T} of the workload's steps")
+                       + " (includes the oracle's two buffer copies)")}
+    if whole and out is not None:
+        g = np.ascontiguousarray(out).view(np.uint8)
+        r = np.ascontiguousarray(res).view(np.uint8)
+        same = g.shape == r.shape and bool(np.array_equal(g, r))
+        line["parity"] = {"T": T, "cells": int(np.asarray(res).size), "bitwise_equal": same}
+    return line
 
 
 def run_reference(args, rank, world):
@@ -388,7 +467,7 @@ def run_reference(args, rank, world):
     return 0
 
 
-def workload_config(name, world):
+def workload_config(name, world, flushed=False):
     ndim, shape, R, dtype, dims, T, post = workload(name)
     div = ""
     if post:
@@ -400,11 +479,60 @@ def workload_config(name, world):
                         f"seeded normalised coefficients, uniform [0,1) field{div}",
             "stencil": name, "dims": list(dims), "T": T, "radius": R,
             "parallelism": f"replicas{world}" if world > 1 else "single",
-            "l2": "inputs larger than L2 (1 GiB+ per buffer vs 129 MB)"}
+            "l2": ("grid inside L2: a 512 MB buffer is written between timed steps (L2 flush), "
+                   "each step timed by its own CUDA events" if flushed else
+                   "inputs larger than L2 (129 MB)")}
 
 
 # ---------------------------------------------------------------------------
 # Our arm.
+
+def sweep_roofline(ndim, shape, R, dtype, post, cells, bt, launch_s, inrun, kernel, traffic=None):
+    """Roofline object of one sweep launch of degree bt over `cells` interior
+    cells taking launch_s seconds: the binding term of min(HBM, shared memory,
+    ALU), the achieved rate in that term's unit, and the same throughput
+    against the roof at the largest degree built for the stencil."""
+    peaks, peak_src = load_measured_peaks()
+    w = bytes_per_cell(dtype)
+    hbm_bytes_launch = cells * 2 * w              # read once + write once per pass
+    flops_launch = cells * bt * flops_per_cell(ndim, shape, R, dtype, post)
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    alu_fp32 = NOMINAL_SMS * NOMINAL_FP32_LANES * 2 * NOMINAL_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
+    alu_peak = alu_fp32 if dtype != "f64" else inrun["fp64_gflops"] / 1e3
+    smem_peak = float(inrun["smem_gbs"])
+    smem_b = smem_bytes_per_cell(ndim, shape, R, dtype, bt)
+    terms = roof_terms(ndim, shape, R, dtype, bt, post, hbm_peak, smem_peak, alu_peak)
+    bound = min(terms, key=terms.get)
+    if bound == "hbm":
+        achieved, peak, unit = hbm_bytes_launch / launch_s / 1e9, hbm_peak, "GB/s"
+    elif bound == "smem":
+        achieved, peak, unit = cells * bt * smem_b / launch_s / 1e9, smem_peak, "GB/s"
+    else:
+        achieved, peak, unit = flops_launch / launch_s / 1e12, alu_peak, "TFLOP/s"
+    roof_gcells = terms[bound] / 1e9
+    measured_gcells = cells * bt / launch_s / 1e9
+    # the same throughput against the roof at the largest degree built for this
+    # stencil: a lower-degree pick cannot hide throughput left on the table
+    bt_top = max(built_degrees(ndim, shape, R, dtype, post) or [bt])
+    terms_top = roof_terms(ndim, shape, R, dtype, bt_top, post, hbm_peak, smem_peak, alu_peak)
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_source": ({"hbm": f"{peak_src} MEASURED_PEAKS.json hbm_gbs",
+                             "smem": "in-run shared-memory microbenchmark (LDS.128)",
+                             "alu": ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if dtype != "f64"
+                                     else "in-run FP64 fma microbenchmark")}[bound]),
+            "kernel": kernel,
+            "algorithmic_bytes_per_launch": hbm_bytes_launch,
+            "algorithmic_flops_per_launch": flops_launch,
+            "smem_bytes_per_cell_update": smem_b,
+            "roof_terms_gcells": {k: v / 1e9 for k, v in terms.items()},
+            "temporal_roof_gcells": roof_gcells,
+            "frac_of_temporal_roof": measured_gcells / roof_gcells,
+            "largest_built_bT": bt_top,
+            "roof_at_largest_bT_gcells": min(terms_top.values()) / 1e9,
+            "roof_at_largest_bT_bound": min(terms_top, key=terms_top.get),
+            "frac_of_roof_at_largest_bT": measured_gcells / (min(terms_top.values()) / 1e9)}
+
 
 def run_ours(args, rank, world, local):
     import torch
@@ -446,21 +574,38 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    # Grids that fit in L2 (the 512^2 case) are timed step by step, with a
+    # write of a buffer larger than L2 between the timed steps; the others
+    # are larger than L2 themselves and run back to back.
+    flush = (torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+             if 3 * x.numel() * x.element_size() < L2_FLUSH_BYTES else None)
     torch.cuda.nvtx.range_push("timed")
-    ev0.record(stream)
-    for _ in range(args.steps):
-        plan.run(x, y, T, stream)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    if flush is None:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.run(x, y, T, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_local = ev0.elapsed_time(ev1)
+    else:
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            plan.run(x, y, T, stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms_local = sum(e0.elapsed_time(e1) for e0, e1 in evs)
     torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     barrier(dist, dev)
     st = plan.status()
     if st != 0:
         raise RuntimeError(f"device status {st}: {an5d.an5d_last_error()}")
-    ms_local = ev0.elapsed_time(ev1)
+    y_host = y.cpu().numpy() if x.numel() * x.element_size() <= (256 << 20) else None
     ms = reduce_max(ms_local, dist, dev)
     ms_step = ms / args.steps
     value = world * cells * T * args.steps / (ms * 1e-3) / 1e9
@@ -481,36 +626,14 @@ def run_ours(args, rank, world, local):
     nbytes = u0.nbytes
 
     # ---- roofline of the dominant kernel (the sweep pass) ----
-    peaks, peak_src = load_measured_peaks()
-    w = bytes_per_cell(dtype)
     launch_s = ms_step * 1e-3 / passes            # halo copy (~us) included: conservative
     full_passes = T // bt
-    hbm_bytes_launch = cells * 2 * w              # read once + write once per pass
-    flops_launch = cells * bt * flops_per_cell(ndim, shape, R, dtype, post)
-    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    alu_fp32 = NOMINAL_SMS * NOMINAL_FP32_LANES * 2 * NOMINAL_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
-    alu_peak = alu_fp32 if dtype != "f64" else inrun["fp64_gflops"] / 1e3
-    t_hbm = hbm_bytes_launch / (hbm_peak * 1e9)
-    t_alu = flops_launch / (alu_peak * 1e12)
-    if t_hbm >= t_alu:
-        bound, achieved, peak, unit = "hbm", hbm_bytes_launch / launch_s / 1e9, hbm_peak, "GB/s"
-    else:
-        bound, achieved, peak, unit = "alu", flops_launch / launch_s / 1e12, alu_peak, "TFLOP/s"
     traffic = committed_traffic(args.workload, bt, cfg["tile_x"])
-    roof_gcells = cells * bt / max(t_hbm, t_alu) / 1e9
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_source": (f"{peak_src} MEASURED_PEAKS.json hbm_gbs" if bound == "hbm" else
-                                ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if dtype != "f64"
-                                 else "in-run FP64 fma microbenchmark")),
-                "kernel": (f"box1_kernel bT={bt}" if ndim == 3 and shape == BOX and R >= 2
-                           else f"sweep{ndim}d_kernel bT={bt} tile_x={cfg['tile_x']}"),
-                "passes_per_step": passes,
-                "full_degree_launches": full_passes,
-                "algorithmic_bytes_per_launch": hbm_bytes_launch,
-                "algorithmic_flops_per_launch": flops_launch,
-                "temporal_roof_gcells": roof_gcells,
-                "frac_of_temporal_roof": (cells * bt / launch_s / 1e9) / roof_gcells}
+    kernel = (f"box1_kernel bT={bt}" if ndim == 3 and shape == BOX and R >= 2
+              else f"sweep{ndim}d_kernel bT={bt} tile_x={cfg['tile_x']}")
+    roofline = sweep_roofline(ndim, shape, R, dtype, post, cells, bt, launch_s, inrun, kernel, traffic)
+    roofline["passes_per_step"] = passes
+    roofline["full_degree_launches"] = full_passes
 
     base = PAPER_V100_GCELLS.get(args.workload)
     line = {
@@ -521,7 +644,7 @@ def run_ours(args, rank, world, local):
         "baseline_note": "paper's V100 SXM2 Tuned figure (Table 5) for this workload: context "
                          "from other hardware" if base else None,
         "dtype": dtype, "data": "synthetic",
-        "config": dict(workload_config(args.workload, world), bT=bt, hsn=cfg["hsn"],
+        "config": dict(workload_config(args.workload, world, flushed=flush is not None), bT=bt, hsn=cfg["hsn"],
                        tile_x=cfg["tile_x"], ctas=cfg["ctas"],
                        model_gcells=cfg["model_gcells"], tuned_gcells=cfg["measured_gcells"]),
         "e2e": {"value": e2e_value, "unit": "GCell-updates/s", "h2d_bytes_per_step": nbytes,
@@ -536,7 +659,7 @@ def run_ours(args, rank, world, local):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_time(ndim, shape, R, dtype, dims, budget_s=args.ref_budget,
-                                            post=post)
+                                            post=post, T_full=T, out=y_host)
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -564,6 +687,7 @@ def run_precision(args, rank, world, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     names = [args.precision_workload] if args.precision_workload else list(PRECISION_WORKLOADS)
+    inrun = an5d.an5d_measure_peaks(stream)
     for name in names:
         ndim, shape, R, recipe, dims, T = PRECISION_WORKLOADS[name]
         n = inputs.coeff_count(ndim, shape, R)
@@ -603,6 +727,11 @@ def run_precision(args, rank, world, local):
                 ms = e0.elapsed_time(e1) / args.steps
             err = an5d.an5d_error_norms(ndim, R, dims, form, y, refs[key], stream)
             umax = float(np.max(np.abs(u0.astype(np.float64))))
+            bt = cfg["bT"]
+            passes = T // bt + (1 if T % bt else 0)
+            roofline = sweep_roofline(ndim, shape, R, form, None, cells, bt, ms * 1e-3 / passes, inrun,
+                                      f"sweep{ndim}d_kernel bT={bt} tile_x={cfg['tile_x']} ({form})")
+            roofline["passes_per_step"] = passes
             line = {"mode": "precision", "workload": name, "form": form,
                     "metric": "GCell-updates/s", "value": cells * T / (ms * 1e-3) / 1e9,
                     "unit": "GCell-updates/s", "ms_per_step": ms, "steps": args.steps,
@@ -610,13 +739,46 @@ def run_precision(args, rank, world, local):
                                "init": "Gaussian bump (sigma n/8) + 0.01 U[0,1)",
                                "coefficients": recipe},
                     "error_vs_fp64": {"max_abs": err["max_abs"], "rel_l2": err["rel_l2"],
-                                      "max_abs_over_max_u0": err["max_abs"] / umax}}
+                                      "max_abs_over_max_u0": err["max_abs"] / umax},
+                    "roofline": roofline}
             if rank == 0:
                 print(json.dumps(line), flush=True)
             del x, y
         refs.clear()
         torch.cuda.empty_cache()
     return 0
+
+
+# degrees the batched kernel builds per radius, largest first
+BATCH_MENU = {1: (8, 4, 1), 2: (4, 2, 1)}
+
+
+def batch_roof(grids, class_bt):
+    """Roof time of one batch step: for every grid, the larger of the HBM time
+    of its passes (each reads and writes the grid once, 8 bytes per cell;
+    the T mod bT remaining steps split greedily over the smaller built
+    degrees, as the kernel runs them) and the time of its flops at the FP32
+    peak, summed over the grids."""
+    peaks, src = load_measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) * 1e9
+    alu = NOMINAL_SMS * NOMINAL_FP32_LANES * 2 * NOMINAL_MAX_MHZ * 1e6
+    bt_of = {(STAR, 1): class_bt[0], (STAR, 2): class_bt[1], (BOX, 1): class_bt[2], (BOX, 2): class_bt[3]}
+    tot = th = ta = 0.0
+    for g in grids:
+        bt = bt_of[(g[0], g[1])]
+        left, passes = g[5] % bt, g[5] // bt
+        for m in BATCH_MENU[g[1]]:
+            if m < bt:
+                passes += left // m
+                left %= m
+        t_h = passes * g[3] * g[4] * 8.0 / hbm
+        t_a = g[3] * g[4] * g[5] * flops_per_cell(2, g[0], g[1], "f32") / alu
+        tot += max(t_h, t_a)
+        th += t_h
+        ta += t_a
+    return {"time_s": tot, "hbm_s": th, "alu_s": ta, "bound": "hbm" if th >= ta else "alu",
+            "class_bt": list(class_bt),
+            "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs; 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
 
 
 def run_batch(args, rank, world, local):
@@ -655,28 +817,24 @@ def run_batch(args, rank, world, local):
         assert b.status() == 0, an5d.an5d_batch_last_error()
         ms = e0.elapsed_time(e1) / args.steps
     cells = info["cell_updates"]
-    # HBM bound: every pass reads and writes each grid once (4 + 4 bytes per cell)
-    peaks, src = load_measured_peaks()
-    passes_bytes = 0.0
-    bt_of = {(STAR, 1): info["class_bt"][0], (STAR, 2): info["class_bt"][1],
-             (BOX, 1): info["class_bt"][2], (BOX, 2): info["class_bt"][3]}
-    menu = {1: (8, 4, 1), 2: (4, 2, 1)}   # built degrees per radius, largest first
-    for g in grids:
-        bt = bt_of[(g[0], g[1])]
-        left, passes = g[5] % bt, g[5] // bt   # remainder split greedily over smaller degrees
-        for m in menu[g[1]]:
-            if m < bt:
-                passes += left // m
-                left %= m
-        passes_bytes += passes * g[3] * g[4] * 8.0
-    t_hbm = passes_bytes / (float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) * 1e9)
-    line = {"mode": "batch", "metric": "GCell-updates/s", "value": cells / (ms * 1e-3) / 1e9,
+    roof = batch_roof(grids, info["class_bt"])
+    top = batch_roof(grids, [BATCH_MENU[1][0], BATCH_MENU[2][0], BATCH_MENU[1][0], BATCH_MENU[2][0]])
+    t = ms * 1e-3
+    line = {"mode": "batch", "metric": "GCell-updates/s", "value": cells / t / 1e9,
             "unit": "GCell-updates/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
             "config": {"grids": len(grids), "cell_updates_per_step": cells, "items": info["items"],
                        "persistent_ctas": info["ctas"], "class_bt": info["class_bt"],
                        "recipe": "sides log-uniform [128,4096], star/box R1-2, T U[10,500], seed 3"},
-            "roofline": {"bound": "hbm", "hbm_time_ms": t_hbm * 1e3, "frac": t_hbm / (ms * 1e-3),
-                         "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs"},
+            "roofline": {"bound": roof["bound"], "roof_time_ms": roof["time_s"] * 1e3,
+                         "hbm_time_ms": roof["hbm_s"] * 1e3, "alu_time_ms": roof["alu_s"] * 1e3,
+                         "frac": roof["time_s"] / t,
+                         "class_bt": info["class_bt"],
+                         "largest_built_class_bt": top["class_bt"],
+                         "roof_at_largest_bT_time_ms": top["time_s"] * 1e3,
+                         "frac_of_roof_at_largest_bT": top["time_s"] / t,
+                         "peak_source": roof["peak_source"],
+                         "how": "per grid max(HBM time of its passes at 8 B per cell and pass, "
+                                "flops at the FP32 peak), summed over the grids"},
             "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
