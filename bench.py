@@ -157,6 +157,7 @@ def built_degrees(ndim, shape, R, dtype, post=None):
         tabs = [(t[0], t[1], t[2], t[5]) for t in K.KERNELS_2D + K.KERNELS_2D_WIDE]
     else:
         tabs = [(t[0], t[1], t[2], t[5]) for t in K.KERNELS_3D]
+        tabs += [(K.STAR, t[0], t[1], "DT_F32") for t in K.KERNELS_3D_STAR]
         tabs += [(K.BOX, t[0], range(1, 2), t[2]) for t in K.KERNELS_3D_BOX1]
     for s2, r2, bts, d2 in tabs:
         if s2 == sh and r2 == R and d2 == dt:

@@ -201,14 +201,14 @@ static int largest_bt(const an5d_plan *p)
 struct PassGeom {
     const KernelEntry *k;
     int tile_stride_x, tiles_x, tile_stride_y, tiles_y, hsn, stream_blocks, units, ctas;
-    // padded column where tile column 0's compute region starts: R in 3D; in
-    // 2D R rounded down to even, so that tiles start on even columns (the 2D
-    // sweep moves 8-byte pairs when rows and tiles are even; the halo column
-    // a radius-1 first tile takes in is never stored)
+    // padded column where tile column 0's compute region starts, chosen so
+    // that tiles start on even columns (the sweeps move 8-byte pairs when
+    // rows and tiles are even): R rounded down to even in 2D, R or R - 1 in
+    // 3D; a halo column the first tile takes in is never stored
     int x_base;
     // 3D: a narrow kernel for the last tile column when the main tiles leave a
     // ragged remainder that fits it (tail_k null otherwise): main columns
-    // cover [R, R + tiles_x * tile_stride_x), the narrow one the rest
+    // cover [x_base, x_base + tiles_x * tile_stride_x), the narrow one the rest
     const KernelEntry *tail_k;
     int tail_stride_x, tail_units;
 };
@@ -250,7 +250,11 @@ static int pass_geometry(const an5d_plan *p, int bt, int hsn_req, PassGeom *g, i
                     p->ndim, p->shape, p->radius, p->dtype, bt);
     const int R = p->radius;
     g->tile_stride_x = g->k->tile_x - 2 * bt * R;
-    g->x_base = p->ndim == 2 ? (R & ~1) : R;
+    // Tiles start on even columns (the tile origin is x_base - bT R; tile
+    // widths and strides are even), so that with an even pitch every row a
+    // lane reads or writes starts on an 8-byte boundary.  The first compute
+    // region may then start one column early, on a halo column it never stores.
+    g->x_base = p->ndim == 2 ? (R & ~1) : R - ((R * (bt - 1)) & 1);
     g->tiles_x = (int)((p->nx + R - g->x_base + g->tile_stride_x - 1) / g->tile_stride_x);
     g->tail_k = nullptr;
     g->tail_stride_x = 0;
@@ -263,7 +267,8 @@ static int pass_geometry(const an5d_plan *p, int bt, int hsn_req, PassGeom *g, i
         KernelKey tk{p->ndim, p->shape, p->radius, p->dtype, bt, p->post, 0};
         tk.part = 1;
         const KernelEntry *t = find_kernel(tk);
-        const int64_t full = p->nx / g->tile_stride_x, rest = p->nx - full * g->tile_stride_x;
+        const int64_t span = p->nx + R - g->x_base;  // columns the tiles cover
+        const int64_t full = span / g->tile_stride_x, rest = span - full * g->tile_stride_x;
         if (t && t->tile_y == g->k->tile_y && full >= 1 && rest > 0 &&
             rest <= t->tile_x - 2 * bt * R) {
             g->tail_k = t;
@@ -640,7 +645,7 @@ static int launch_pass(const an5d_plan *p, int bt, const void *src, void *dst, c
     PassDesc dt = d;
     if (int s = encode_row_map(&dt.tmap, src, p->dtype, p->total, g.tail_k->tile_x + A)) return s;
     dt.tile_stride_x = g.tail_stride_x;
-    dt.x_base = p->radius + g.tiles_x * g.tile_stride_x;
+    dt.x_base = g.x_base + g.tiles_x * g.tile_stride_x;
     dt.tiles_x = 1;
     dt.total_units = g.tail_units;
     dt.ctas = g.tail_units;

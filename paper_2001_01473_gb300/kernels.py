@@ -65,10 +65,7 @@ KERNELS_DIV_2D_WIDE = [
 # tile (tile cells x (2R+1) planes x bT levels) must fit in one SM's
 # register file, which bounds the tile height for a given degree.
 KERNELS_3D = [
-    (STAR, 1, range(1, 4), "float", "MODE_PLAIN", "DT_F32", 16),
-    (STAR, 1, range(4, 5), "float", "MODE_PLAIN", "DT_F32", 8),
     (STAR, 2, range(1, 2), "float", "MODE_PLAIN", "DT_F32", 16),
-    (STAR, 2, range(2, 3), "float", "MODE_PLAIN", "DT_F32", 12),
     (STAR, 3, range(1, 2), "float", "MODE_PLAIN", "DT_F32", 16),
     (STAR, 4, range(1, 2), "float", "MODE_PLAIN", "DT_F32", 16),
     (BOX, 1, range(1, 3), "float", "MODE_PLAIN", "DT_F32", 16),
@@ -80,6 +77,28 @@ KERNELS_3D = [
     (BOX, 1, range(1, 2), "double", "MODE_PLAIN", "DT_F64", 12),
     (STAR, 1, range(1, 4), "__half", "MODE_PLAIN", "DT_F16S", 16),
     (STAR, 1, range(1, 4), "float", "MODE_DOT2", "DT_F32C", 16),
+]
+
+
+# FP32 3D stars on the sweep with one CTA barrier per plane
+# (sweep3d_star.cuh): (radius, bT range, warps per CTA, rows per warp).  Tiles
+# are 128 cells wide and (warps x rows per warp) rows high; radius 1 and 2
+# also get the narrow last-column instance (R cells per lane, same rows).
+# The level rings take bT (2R+1) 4 RW registers per thread and the published
+# planes bT (R+1) planes of shared memory, so the higher degrees and radii
+# run on fewer, fatter threads (12 warps: 170 registers per thread, 8 warps:
+# 255).  At bT = 1 the radius 2-4 stars measured faster on the
+# per-level-exchange sweep (395 / 272 / 199 against 360 / 227 / 110 GCell/s
+# on 512^3), which keeps those degrees.  The radius-4 star at bT 2 spills
+# part of its rings (no tile of this shape holds them in registers) and is
+# built for the tuner to time.
+KERNELS_3D_STAR = [
+    (1, range(1, 4), 16, 2),
+    (1, range(4, 5), 12, 2),
+    (2, range(2, 3), 12, 2),
+    (2, range(3, 4), 8, 3),
+    (3, range(2, 3), 8, 3),
+    (4, range(2, 3), 12, 2),
 ]
 
 
@@ -153,6 +172,12 @@ def instantiations():
             tv = tail3d(shape, r, s, mode)
             if tv and tv < v:
                 yield "sweep3d.cuh", f"entry3d<{shape}, {r}, {bt}, {s}, {mode}, {nw}, POST_NONE, {tv}, {rw}, 1>({dt})"
+    for r, bts, nw, rw in KERNELS_3D_STAR:
+        for bt in bts:
+            yield "sweep3d_star.cuh", f"entry_star3d<{r}, {bt}, {nw}, 4, {rw}, 0>()"
+            tv = tail3d(STAR, r, "float", "MODE_PLAIN")
+            if tv and tv < 4:
+                yield "sweep3d_star.cuh", f"entry_star3d<{r}, {bt}, {nw}, {tv}, {rw}, 1>()"
     for r, s, dt, nw, rw in KERNELS_3D_BOX1:
         yield "sweep3d_box1.cuh", f"entry_box1<{r}, {s}, {nw}, {rw}>({dt})"
     for post in POSTS:

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2001_01473_gb300 import an5d, inputs
-from paper_2001_01473_gb300.kernels import KERNELS_3D, KERNELS_3D_BOX1
+from paper_2001_01473_gb300.kernels import KERNELS_3D, KERNELS_3D_BOX1, KERNELS_3D_STAR
 from _gpu_util import assert_bitwise, coeffs_for, gpu_run, oracle_run
 
 pytestmark = pytest.mark.gpu
@@ -15,6 +15,8 @@ SH = {"SH_STAR": STAR, "SH_BOX": BOX}
 BUILT = {}
 for _sh, _r, _bts, _s, _m, _dt, _nw in KERNELS_3D:
     BUILT.setdefault((SH[_sh], _r, DT[_dt]), []).extend(list(_bts))
+for _r, _bts, _nw, _rw in KERNELS_3D_STAR:
+    BUILT.setdefault((STAR, _r, "f32"), []).extend(list(_bts))
 for _r, _s, _dt, _nw, _rw in KERNELS_3D_BOX1:
     BUILT.setdefault((BOX, _r, DT[_dt]), []).append(1)
 CASES = [(shape, R, dt, bt) for (shape, R, dt), bts in sorted(BUILT.items()) for bt in bts]
@@ -131,9 +133,13 @@ def test_narrow_last_column(shape, R, bt, rest):
     per pass); one cell wider, or none at all, stays on full tiles.
     Bit-exact either way."""
     tsx, ts_narrow = 128 - 2 * bt * R, 32 * R - 2 * bt * R
-    # two full columns plus the remainder
+    # two full columns plus the remainder; tiles start on even columns, so
+    # when R (bT - 1) is odd the first compute region starts one column early
+    # (on the halo column) and the tiles cover one column more than the
+    # interior
+    early = (R * (bt - 1)) & 1
     rest = {"narrow": ts_narrow, "narrow+1": ts_narrow + 1, "one": 1, "none": 0}[rest]
-    nx = 2 * tsx + rest
+    nx = 2 * tsx + rest - early
     dims = (9, 30, nx)
     c = coeffs_for(3, shape, R, seed=3)
     u0 = inputs.field(dims, R, 2, "f32")
