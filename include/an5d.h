@@ -293,6 +293,36 @@ int an5d_error_norms(int ndim, int radius, const int64_t *dims, an5d_dtype dtype
 int an5d_run_adjoint(an5d_plan *plan, const void *u0, const void *gT, void *grad_u0,
                      double *grad_coeffs, int64_t T, void *stream);
 
+/* Halo-deepened domain split (Section 2.3's overlapped tiling applied to
+ * slabs of the grid; the per-device step of a multi-GPU decomposition).
+ * The slowest axis (y in 2D, z in 3D) of the interior is cut into nsub
+ * slabs as evenly as possible (the first extent % nsub slabs own one plane
+ * more).  Slab k owns interior planes [a, b) (0-based interior index) and
+ * holds the padded planes [lo, hi) = [a - bT R, b + bT R + 2R) clipped to
+ * the padded array: bT R ghost planes beyond its owned planes and R outer
+ * planes that act as a fixed halo during a pass.
+ *
+ * an5d_split_geometry: host only (no device needed).  out: host array of 4
+ *   int64, receives {a, b, lo, hi} of slab k.  AN5D_ERR_INVALID_ARG on bad
+ *   arguments; AN5D_ERR_UNSUPPORTED if a slab would own fewer than
+ *   bT R + R planes (its ghost planes would reach past its neighbour).
+ *
+ * an5d_run_split: the plan's sweep of T steps (its degree bT and stream
+ *   block length) run as nsub slabs on the calling device: per pass of
+ *   degree d <= bT, every slab runs one pass of its own padded array; then
+ *   every plane a slab holds but does not own is copied from the slab that
+ *   owns it (the one exchange per pass), and at the end the owned planes are
+ *   gathered into `out`.  in, out as for an5d_run (device, padded, plan
+ *   dtype; `in` is not written).  The result is bit for bit that of
+ *   an5d_run.  Allocates nsub slab plans and 2 nsub slab buffers for the
+ *   call and frees them before returning; synchronous on `stream`.  Plain
+ *   stencils (no per-step division) only: AN5D_ERR_UNSUPPORTED otherwise.
+ *   nsub = 1 or T = 0 is an5d_run.  (The paper's host code runs one grid on
+ *   one device; the exchange between devices is not built: one GPU.) */
+int an5d_split_geometry(int ndim, const int64_t *dims, int radius, int bt, int nsub, int k,
+                        int64_t *out);
+int an5d_run_split(an5d_plan *plan, int nsub, const void *in, void *out, int64_t T, void *stream);
+
 /* ------------------------------------------------------------------------
  * Batched form: many independent 2D FP32 grids of uneven size, stencil and
  * length in one persistent launch replayed as a CUDA graph.  (No counterpart

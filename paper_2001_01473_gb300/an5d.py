@@ -143,6 +143,10 @@ def load(path: str = LIB_PATH):
     L.an5d_batch_inject_stall.restype = I
     L.an5d_run_adjoint.argtypes = [P, P, P, P, P, I64, P]
     L.an5d_run_adjoint.restype = I
+    L.an5d_split_geometry.argtypes = [I, P, I, I, I, I, P]
+    L.an5d_split_geometry.restype = I
+    L.an5d_run_split.argtypes = [P, I, P, P, I64, P]
+    L.an5d_run_split.restype = I
     L.an5d_batch_plan_create.argtypes = [I, P]
     L.an5d_batch_plan_create.restype = P
     L.an5d_batch_tune.argtypes = [P, P]
@@ -271,6 +275,21 @@ def an5d_run_adjoint(plan: int, u0, gT, grad_u0, T: int, stream=None) -> np.ndar
     _check(load().an5d_run_adjoint(plan, _ptr(u0), _ptr(gT), _ptr(grad_u0), gc.ctypes.data,
                                    int(T), _stream(stream)))
     return gc
+
+
+def an5d_split_geometry(ndim: int, dims, radius: int, bT: int, nsub: int, k: int) -> dict:
+    """Slab k of an nsub-way split along the slowest axis (see an5d.h):
+    owned interior planes [a, b) and the padded planes [lo, hi) it holds."""
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int64))
+    out = np.zeros(4, dtype=np.int64)
+    _check(load().an5d_split_geometry(ndim, d.ctypes.data, radius, bT, nsub, k, out.ctypes.data))
+    return {"a": int(out[0]), "b": int(out[1]), "lo": int(out[2]), "hi": int(out[3])}
+
+
+def an5d_run_split(plan: int, nsub: int, inp, out, T: int, stream=None) -> int:
+    """The plan's sweep as nsub slabs with deepened halos (see an5d.h)."""
+    return _check(load().an5d_run_split(plan, int(nsub), _ptr(inp), _ptr(out), int(T),
+                                        _stream(stream)))
 
 
 def an5d_plan_inject_stall(plan: int, enable: bool) -> int:
