@@ -62,5 +62,9 @@ def test_precision_forms_error_vs_fp64_oracle(ndim, shape, dims, T):
         u, g = 2.0 ** -24, n * 2.0 ** -24 / (1 - n * 2.0 ** -24)
         bound = {"f32": T * g, "f32c": T * (u + g * g), "f16": T * (2.0 ** -11 + g)}[form] * umax
         assert errs[form] <= bound, (form, errs[form], bound)
-    assert errs["f32c"] < errs["f32"]          # compensation helps
+    # Dot2 is the more accurate form in this regime: small grids and runs of
+    # a few hundred steps, where the error is the sum of per-step roundings
+    # (one Dot2 step is correctly rounded).  On long runs over large smooth
+    # fields the plain chain can end closer to FP64 (the benchmark reports it).
+    assert errs["f32c"] < errs["f32"]
     assert errs["f16"] > errs["f32"]           # binary16 storage costs accuracy
