@@ -842,17 +842,61 @@ def run_batch(args, rank, world, local):
     return 0
 
 
+ADJ_NB = {1: 4, 2: 2}   # block degree of the batched adjoint per radius
+
+
+def adjoint_roof(grids):
+    """Roof time of one batched-adjoint step: per grid, the larger of its
+    algorithmic HBM time and its flops at the FP32 peak, summed.  Per block
+    of nb steps (M = ceil(T/nb) blocks) a grid's cells move: 8 B for the
+    forward checkpoint pass (M - 1 of them), 4 + 4 (nb - 1) B for the
+    recompute pass (read the checkpoint, write nb - 1 states; nb >= 2), and
+    8 + 4 nb B for the transposed pass (read and write g, read the nb
+    states); flops: (2n - 1) per cell and step of every forward, recompute
+    and transposed step, and 2n per cell and step of the coefficient
+    gradient."""
+    peaks, src = load_measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) * 1e9
+    alu = NOMINAL_SMS * NOMINAL_FP32_LANES * 2 * NOMINAL_MAX_MHZ * 1e6
+    tot = th = ta = 0.0
+    for shape, R, _c, ny, nx, T in grids:
+        cells = float(ny * nx)
+        n = inputs.coeff_count(2, shape, R)
+        nb = ADJ_NB[R]
+        M = -(-T // nb)
+        byt = 8.0 * max(M - 1, 0)
+        fl = (2 * n - 1) * nb * max(M - 1, 0)
+        for m in range(M):
+            nbm = min(nb, T - m * nb)
+            if nbm >= 2:
+                byt += 4 + 4 * (nbm - 1)
+                fl += (2 * n - 1) * (nbm - 1)
+            byt += 8 + 4 * nbm
+            fl += nbm * (2 * n - 1 + 2 * n)
+        t_h, t_a = cells * byt / hbm, cells * fl / alu
+        tot += max(t_h, t_a)
+        th += t_h
+        ta += t_a
+    return {"time_s": tot, "hbm_s": th, "alu_s": ta, "bound": "hbm" if th >= ta else "alu",
+            "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs; 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+
+
 def run_adjoint_bench(args, rank, world, local):
     """Adjoint form on the batched workload: loss 0.5 ||u_T - target||^2 per
     grid (target uniform [0,1) from seed 2), gradients w.r.t. u_0 and the
-    coefficients by the checkpointed adjoint; timed over all 512 grids."""
+    coefficients for all 512 grids by the batched adjoint (persistent
+    launches in one CUDA graph), and for comparison by the single-grid
+    adjoint driven per grid from host threads.  The CPU-baseline leg runs
+    the FP64 oracle adjoint on a sample of the grids, timed, and reports the
+    GPU result's error against it."""
     import torch
     from paper_2001_01473_gb300 import an5d
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    descs = inputs.batch_descs()
-    grids, plans, xs, gts = [], [], [], []
+    descs = inputs.batch_descs(n=args.batch_n, side_hi=args.batch_side_hi, t_lo=args.batch_tlo,
+                               t_hi=args.batch_thi)
+    grids, xs, gts = [], [], []
     for i, d in enumerate(descs):
         n = inputs.coeff_count(2, d.shape, d.radius)
         c = inputs.normalised_coeffs(n, 100 + i)
@@ -865,54 +909,127 @@ def run_adjoint_bench(args, rank, world, local):
         b.run(xs, ys, stream)
         torch.cuda.synchronize()
         assert b.status() == 0
+    targets = []
     for i, g in enumerate(grids):
         R = g[1]
         tg = torch.from_numpy(inputs.target_field((g[3], g[4]), R, 2, "f32")).to(dev)
         gt = torch.zeros_like(ys[i])
         gt[R:-R, R:-R] = ys[i][R:-R, R:-R] - tg[R:-R, R:-R]
         gts.append(gt)
-        plans.append(an5d.Plan(2, g[0], R, g[2], "f32", (g[3], g[4])))
+        targets.append(tg)
     del ys
     gus = [torch.empty_like(x) for x in xs]
     cells = sum(float(g[3] * g[4] * g[5]) for g in grids)
-    # Grids are independent: host threads drive them on their own streams so
-    # that the small grids' launches overlap (each call synchronises only its
-    # stream).  Largest work first, taken from a shared queue.
-    import concurrent.futures
-    import threading
-    order = sorted(range(len(grids)), key=lambda i: -grids[i][3] * grids[i][4] * grids[i][5])
-    streams = [torch.cuda.Stream(device=dev) for _ in range(args.adjoint_streams)]
-    times = []
-    for rep in range(max(1, args.steps)):
+    with an5d.AdjointBatch(grids, int(args.adjoint_budget_gib * (1 << 30))) as ab:
+        info = ab.info()
+        for _ in range(max(1, args.warmup)):
+            dc = ab.run(xs, gts, gus, stream)
         torch.cuda.synchronize()
-        nxt = iter(order)
-        lock = threading.Lock()
-
-        def worker(k):
-            torch.cuda.set_device(local)
-            st = streams[k]
-            while True:
-                with lock:
-                    i = next(nxt, None)
-                if i is None:
-                    return
-                an5d.an5d_run_adjoint(plans[i].handle, xs[i], gts[i], gus[i], grids[i][5], st)
-
-        t0 = time.perf_counter()
-        with concurrent.futures.ThreadPoolExecutor(len(streams)) as ex:
-            list(ex.map(worker, range(len(streams))))
+        clocks = ClockSampler(local)
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            dc = ab.run(xs, gts, gus, stream)      # synchronous: includes the dL/dc copy to the host
+        e1.record(stream)
         torch.cuda.synchronize()
-        times.append(time.perf_counter() - t0)
-    t = min(times)
-    for p in plans:
-        p.close()
+        clk = clocks.stop()
+        t = e0.elapsed_time(e1) * 1e-3 / args.steps
+    # the single-grid adjoint (checkpointed level-storing passes and a
+    # separate reduction per block) driven per grid from host threads, each
+    # on its own stream, largest work first: the same gradients by another
+    # schedule, timed for comparison
+    per_grid = None
+    if args.adjoint_streams > 0:
+        import concurrent.futures
+        import threading
+        plans = [an5d.Plan(2, g[0], g[1], g[2], "f32", (g[3], g[4])) for g in grids]
+        order = sorted(range(len(grids)), key=lambda i: -grids[i][3] * grids[i][4] * grids[i][5])
+        streams = [torch.cuda.Stream(device=dev) for _ in range(args.adjoint_streams)]
+        gus2 = [torch.empty_like(x) for x in xs]
+        times = []
+        for _rep in range(2):  # the first run grows the plans' work memory
+            torch.cuda.synchronize()
+            nxt = iter(order)
+            lock = threading.Lock()
+
+            def worker(k):
+                torch.cuda.set_device(local)
+                while True:
+                    with lock:
+                        i = next(nxt, None)
+                    if i is None:
+                        return
+                    an5d.an5d_run_adjoint(plans[i].handle, xs[i], gts[i], gus2[i], grids[i][5], streams[k])
+
+            t0 = time.perf_counter()
+            with concurrent.futures.ThreadPoolExecutor(len(streams)) as ex:
+                list(ex.map(worker, range(len(streams))))
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        for pl in plans:
+            pl.close()
+        same = all(torch.equal(a, b) for a, b in zip(gus, gus2))
+        per_grid = {"value": cells / times[-1] / 1e9, "unit": "GCell-updates/s", "seconds_per_step": times[-1],
+                    "streams": args.adjoint_streams, "grad_u0_bit_identical_to_batched": same,
+                    "how": "an5d_run_adjoint per grid from host threads, one CUDA stream each, largest first "
+                           "(host wall clock)"}
+        del gus2
+    roof = adjoint_roof(grids)
     line = {"mode": "adjoint", "metric": "GCell-updates/s", "value": cells / t / 1e9,
-            "unit": "GCell-updates/s", "seconds_per_step": t, "steps": len(times),
-            "config": {"grids": len(grids), "cell_updates_per_step": cells,
+            "unit": "GCell-updates/s", "seconds_per_step": t, "steps": args.steps, "warmup": args.warmup,
+            "config": {"grids": len(grids), "cell_updates_per_step": cells, "items": info["items"],
+                       "waves": info["waves"], "work_gib": info["work_bytes"] / (1 << 30),
+                       "persistent_ctas": info["ctas"], "class_nb": info["class_nb"],
                        "loss": "0.5*||u_T - target||^2, target U[0,1) seed 2",
-                       "schedule": "checkpoint every bT (<= 4) steps; per block: blocked "
-                                   "recompute + blocked transposed pass + coefficient reduction",
-                       "streams": args.adjoint_streams}}
+                       "schedule": "checkpoint every nb steps (nb 4 for radius 1, 2 for radius 2); "
+                                   "per block: blocked recompute storing the block's states + blocked "
+                                   "transposed pass accumulating dL/dc in registers; all grids in "
+                                   "persistent launches of one CUDA graph"},
+            "roofline": {"bound": roof["bound"], "roof_time_ms": roof["time_s"] * 1e3,
+                         "hbm_time_ms": roof["hbm_s"] * 1e3, "alu_time_ms": roof["alu_s"] * 1e3,
+                         "frac": roof["time_s"] / t, "peak_source": roof["peak_source"],
+                         "how": "per grid max(algorithmic HBM bytes of its forward, recompute and "
+                                "transposed passes, flops of those passes and of dL/dc at the FP32 "
+                                "peak), summed over the grids"},
+            "clocks": clk}
+    if per_grid is not None:
+        line["per_grid_host_driven"] = per_grid
+    if not args.no_cpu_baseline and rank == 0:
+        # CPU-baseline leg: the FP64 oracle adjoint on the grids with the
+        # fewest cell-updates (a bounded sample), timed; the GPU gradients of
+        # those grids against it
+        import oracle
+        order = sorted(range(len(grids)), key=lambda i: grids[i][3] * grids[i][4] * grids[i][5])
+        sample, t_cpu, cells_cpu = [], 0.0, 0.0
+        err_u, err_c = 0.0, 0.0
+        for i in order:
+            shape, R, c, ny, nx, T = grids[i]
+            if t_cpu > args.ref_budget or len(sample) >= 24:
+                break
+            c32 = c.astype(np.float32).astype(np.float64)
+            u0 = xs[i].cpu().numpy().astype(np.float64)
+            tg = targets[i].cpu().numpy().astype(np.float64)
+            t0 = time.perf_counter()
+            _loss, ref_gu, ref_gc = oracle.adjoint_f64(2, shape, R, c32, (ny, nx), u0, tg, T)
+            t_cpu += time.perf_counter() - t0
+            cells_cpu += float(ny * nx * T)
+            inner = (slice(R, R + ny), slice(R, R + nx))
+            gu = gus[i].cpu().numpy()[inner].astype(np.float64)
+            n = len(c)
+            e_u = float(np.linalg.norm(gu - ref_gu[inner]) / max(np.linalg.norm(ref_gu[inner]), 1e-300))
+            e_c = float(np.linalg.norm(dc[i][:n] - ref_gc) / max(np.linalg.norm(ref_gc), 1e-300))
+            err_u, err_c = max(err_u, e_u), max(err_c, e_c)
+            sample.append(i)
+        line["cpu_baseline"] = {"value": cells_cpu / t_cpu / 1e9, "unit": "GCell-updates/s",
+                                "cores": oracle.get_threads(), "kind": "oracle", "seconds": t_cpu,
+                                "sample": f"FP64 oracle adjoint (forward + backward) of the {len(sample)} "
+                                          f"grids with the fewest cell-updates ({cells_cpu:.3g} of them)"}
+        line["error_vs_fp64_oracle"] = {"grids": len(sample), "max_rel_l2_grad_u0": err_u,
+                                        "max_rel_l2_grad_coeffs": err_c,
+                                        "note": "the oracle starts from the same FP32 inputs and the "
+                                                "run's FP32-rounded coefficients"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -940,7 +1057,9 @@ def main():
     ap.add_argument("--batch", action="store_true", help="report the batched form (512 grids)")
     ap.add_argument("--adjoint", action="store_true", help="report the adjoint form (512 grids)")
     ap.add_argument("--adjoint-streams", type=int, default=8,
-                    help="host threads / CUDA streams driving the adjoint grids")
+                    help="host threads / streams of the per-grid adjoint leg (0: skip it)")
+    ap.add_argument("--adjoint-budget-gib", type=float, default=200.0,
+                    help="device work memory of the batched adjoint (grids beyond it run in later waves)")
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-side-hi", type=int, default=4096)
     ap.add_argument("--batch-tlo", type=int, default=10)

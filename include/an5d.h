@@ -465,6 +465,58 @@ int an5d_paper_model(const an5d_paper_stencil *st, const int64_t *dims, int bT, 
  * in this process, else nominal figures from the device attributes. */
 int an5d_get_peaks(an5d_peaks *out);
 
+/* ------------------------------------------------------------------------
+ * Batched adjoint: dL/du_0 and dL/dc for many independent 2D FP32 grids
+ * (the grids of an an5d_grid_desc batch) in persistent launches replayed
+ * as one CUDA graph.  (No counterpart in the paper: the adjoint follows from
+ * differentiating the time loop of Section 3.3.)  Per grid, with block
+ * degree nb (4 for radius 1, 2 for radius 2) and M = ceil(T / nb) blocks:
+ * forward passes store checkpoints u_{m nb}; then for each block, last
+ * first, one pass recomputes the block's states from its checkpoint and
+ * stores them, and one temporally blocked pass of the transposed stencil
+ * (offsets -o_k, zero halo) takes g through the block while adding
+ * g_{t+1}[p] u_t[p + o_k] to the coefficient gradient in registers.
+ * g_t = S^T g_{t+1}; dL/dc_k = sum_t sum_p g_{t+1}[p] u_t[p + o_k].
+ * ------------------------------------------------------------------------ */
+
+typedef struct an5d_adjoint_batch an5d_adjoint_batch;
+
+typedef struct {
+    int grids;
+    int waves;             /* persistent launches per run (work memory within the budget) */
+    int ctas;              /* persistent CTAs per launch */
+    int64_t items;         /* (grid, x tile, stream block, pass) work items, all waves */
+    double cell_updates;   /* sum over grids of ny * nx * T */
+    size_t work_bytes;     /* device work memory owned by the batch (the largest wave's) */
+    int class_nb[4];       /* block degree per class: star R1, star R2, box R1, box R2 */
+} an5d_adjoint_batch_info_t;
+
+/* Create: copies descs and coefficients (rounded to FP32), plans the work
+ * items, and splits the grids, in order, into waves whose work memory
+ * (T/nb checkpoints, nb - 1 level grids, one g grid and per-tile partial
+ * sums per grid) fits budget_bytes (0: 48 GiB); a grid larger than the
+ * budget gets a wave of its own.  Allocates the largest wave's work memory
+ * on the current device.  Returns NULL on failure (message:
+ * an5d_adjoint_batch_last_error). */
+an5d_adjoint_batch *an5d_adjoint_batch_create(int n, const an5d_grid_desc *descs, size_t budget_bytes);
+
+/* Run: u0s[i] device, grid i's forward input (padded FP32, halo = the
+ * Dirichlet boundary); gTs[i] device, dL/du_T (padded; its halo is
+ * ignored); grad_u0s[i] device output, dL/du_0 on the interior and 0 on the
+ * halo (must not overlap u0s[i] or gTs[i]); grad_coeffs host output, n rows
+ * of 25 doubles, row i holding grid i's dL/dc_k in canonical order (the
+ * rest zero).  The coefficient gradient is summed in FP32 per warp over a
+ * fixed partition and in FP64 across warps and tiles, in a fixed order:
+ * deterministic.  The first call with a set of buffers captures the graph
+ * (later calls with the same buffers replay it).  Synchronous on `stream`.
+ * AN5D_ERR_TIMEOUT if a bounded device wait gave up (the context stays
+ * usable).  Every wait is bounded; nothing traps or hangs. */
+int an5d_adjoint_batch_run(an5d_adjoint_batch *ab, const void *const *u0s, const void *const *gTs,
+                           void *const *grad_u0s, double *grad_coeffs, void *stream);
+int an5d_adjoint_batch_info(const an5d_adjoint_batch *ab, an5d_adjoint_batch_info_t *info);
+void an5d_adjoint_batch_destroy(an5d_adjoint_batch *ab);
+const char *an5d_adjoint_batch_last_error(void);
+
 /* Message and status of the last failure on the calling thread. */
 const char *an5d_last_error(void);
 int an5d_last_status(void);

@@ -83,6 +83,17 @@ class an5d_batch_info_t(ctypes.Structure):
                 "cell_updates": self.cell_updates, "class_bt": list(self.class_bt)}
 
 
+class an5d_adjoint_batch_info_t(ctypes.Structure):
+    _fields_ = [("grids", ctypes.c_int), ("waves", ctypes.c_int), ("ctas", ctypes.c_int),
+                ("items", ctypes.c_int64), ("cell_updates", ctypes.c_double),
+                ("work_bytes", ctypes.c_size_t), ("class_nb", ctypes.c_int * 4)]
+
+    def as_dict(self) -> dict:
+        return {"grids": self.grids, "waves": self.waves, "ctas": self.ctas, "items": self.items,
+                "cell_updates": self.cell_updates, "work_bytes": self.work_bytes,
+                "class_nb": list(self.class_nb)}
+
+
 class an5d_peaks(ctypes.Structure):
     _fields_ = [("hbm_gbs", ctypes.c_double), ("fp32_gflops", ctypes.c_double),
                 ("fp64_gflops", ctypes.c_double), ("smem_gbs", ctypes.c_double),
@@ -165,6 +176,16 @@ def load(path: str = LIB_PATH):
     L.an5d_batch_last_error.restype = ctypes.c_char_p
     L.an5d_batch_plan_destroy.argtypes = [P]
     L.an5d_batch_plan_destroy.restype = None
+    L.an5d_adjoint_batch_create.argtypes = [I, P, ctypes.c_size_t]
+    L.an5d_adjoint_batch_create.restype = P
+    L.an5d_adjoint_batch_run.argtypes = [P, P, P, P, P, P]
+    L.an5d_adjoint_batch_run.restype = I
+    L.an5d_adjoint_batch_info.argtypes = [P, ctypes.POINTER(an5d_adjoint_batch_info_t)]
+    L.an5d_adjoint_batch_info.restype = I
+    L.an5d_adjoint_batch_destroy.argtypes = [P]
+    L.an5d_adjoint_batch_destroy.restype = None
+    L.an5d_adjoint_batch_last_error.argtypes = []
+    L.an5d_adjoint_batch_last_error.restype = ctypes.c_char_p
     L.an5d_measure_peaks.argtypes = [ctypes.POINTER(an5d_peaks), P]
     L.an5d_measure_peaks.restype = I
     L.an5d_get_peaks.argtypes = [ctypes.POINTER(an5d_peaks)]
@@ -551,6 +572,85 @@ class Batch:
     def close(self) -> None:
         if self.handle:
             an5d_batch_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Batched adjoint.
+
+def an5d_adjoint_batch_last_error() -> str:
+    return load().an5d_adjoint_batch_last_error().decode()
+
+
+def _acheck(rc: int) -> int:
+    if rc != AN5D_OK:
+        raise An5dError(rc, an5d_adjoint_batch_last_error())
+    return rc
+
+
+def an5d_adjoint_batch_create(grids, budget_bytes: int = 0) -> tuple:
+    """grids: list of (shape, radius, coeffs, ny, nx, T).  Returns (handle, keepalive)."""
+    keep = [np.ascontiguousarray(np.asarray(g[2], dtype=np.float64)) for g in grids]
+    arr = (an5d_grid_desc * len(grids))()
+    for i, g in enumerate(grids):
+        arr[i] = an5d_grid_desc(int(g[0]), int(g[1]), keep[i].ctypes.data, int(g[3]), int(g[4]),
+                                int(g[5]))
+    h = load().an5d_adjoint_batch_create(len(grids), ctypes.cast(arr, ctypes.c_void_p), int(budget_bytes))
+    if not h:
+        raise An5dError(AN5D_ERR_INVALID_ARG, an5d_adjoint_batch_last_error())
+    return h, (keep, arr)
+
+
+def an5d_adjoint_batch_run(ab: int, u0s, gTs, grad_u0s, stream=None) -> np.ndarray:
+    """Returns dL/dc as an (n, 25) float64 array (row i: grid i, canonical order)."""
+    n = len(u0s)
+    pu = (ctypes.c_void_p * n)(*[_ptr(x) for x in u0s])
+    pg = (ctypes.c_void_p * n)(*[_ptr(x) for x in gTs])
+    po = (ctypes.c_void_p * n)(*[_ptr(x) for x in grad_u0s])
+    dc = np.zeros((n, 25), dtype=np.float64)
+    _acheck(load().an5d_adjoint_batch_run(ab, ctypes.cast(pu, ctypes.c_void_p), ctypes.cast(pg, ctypes.c_void_p),
+                                          ctypes.cast(po, ctypes.c_void_p), dc.ctypes.data, _stream(stream)))
+    return dc
+
+
+def an5d_adjoint_batch_info(ab: int) -> dict:
+    info = an5d_adjoint_batch_info_t()
+    _acheck(load().an5d_adjoint_batch_info(ab, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def an5d_adjoint_batch_destroy(ab: int) -> None:
+    load().an5d_adjoint_batch_destroy(ab)
+
+
+class AdjointBatch:
+    """RAII wrapper of a batched adjoint; grids = [(shape, radius, coeffs, ny, nx, T), ...]."""
+
+    def __init__(self, grids, budget_bytes: int = 0):
+        self.grids = list(grids)
+        self.handle, self._keep = an5d_adjoint_batch_create(self.grids, budget_bytes)
+
+    def run(self, u0s, gTs, grad_u0s, stream=None) -> np.ndarray:
+        return an5d_adjoint_batch_run(self.handle, u0s, gTs, grad_u0s, stream)
+
+    def info(self) -> dict:
+        return an5d_adjoint_batch_info(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            an5d_adjoint_batch_destroy(self.handle)
             self.handle = 0
 
     def __enter__(self):

@@ -103,13 +103,6 @@ __device__ __forceinline__ bool batch_dispatch_deg(int deg, const Tile2D &tg, co
     return batch_tile<SHAPE, R, 1>(tg, map, dst, status, ring, gc);
 }
 
-__device__ __forceinline__ int ld_acquire(const int *p)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __global__ void __launch_bounds__(BATCH_WARPS * 32)
     batch_kernel(const BatchGrid *__restrict__ grids, const BatchItem *__restrict__ items, int n_items,
                  int *queue, int *counters, int *status, int *abort_flag, int stall_item)

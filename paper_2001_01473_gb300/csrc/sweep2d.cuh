@@ -121,6 +121,15 @@ struct Tile2D {
     int stall;     // fault injection (tests only): the first row's wait cannot complete
 };
 
+// Default row observer of sweep2d_tile: none.  A row observer sees every
+// interior row of levels 0..BT-1 as it is produced (level 0: the staged input
+// row), with the warp's V cells per lane; the adjoint's coefficient gradient
+// accumulates its products there.  Called by all 32 lanes.
+struct NoRowHook {
+    static constexpr bool active = false;
+    template <typename C, int V> __device__ __forceinline__ void row(int, int, const C (&)[V]) {}
+};
+
 // One warp advances one tile of one stream block by BT time levels: it
 // streams the source rows through its TMA ring and level registers and
 // stores the level-BT rows [y0, y1) x [sc0, sc1).  The caller owns the
@@ -131,17 +140,19 @@ struct Tile2D {
 // With RAW the rows are fetched by non-tensor bulk copies from tg.src
 // (clamped to the array; the array's last partial 16-byte chunk by plain
 // loads) instead of through the tensor map: no descriptor to fetch, for
-// callers that switch arrays often.  With POST (division-type stencils) every
+// callers that switch arrays often.  HOOK (scalar paths) observes the interior
+// rows of levels 0..BT-1 (NoRowHook: none).  With POST (division-type stencils) every
 // level's weighted sum is divided by post_c, or multiplied by it when post_c
 // is the reciprocal (post_p: the pair (post_c, post_c)).  Returns false if a
 // bounded wait gave up.
 template <int SHAPE, int R, int BT, typename S, int MODE, bool PACK, typename CF, typename CP,
-          bool LEVELS = false, bool RAW = false, int POST = POST_NONE, int V_ = CELLS_PER_LANE>
+          bool LEVELS = false, bool RAW = false, int POST = POST_NONE, int V_ = CELLS_PER_LANE,
+          typename HOOK = NoRowHook>
 __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap *tmap, S *const dst,
                                              int *const status, unsigned char *const ring,
                                              const CF &cf, const CP &cp, S *const *lvl = nullptr,
                                              const typename StorageTraits<S>::C post_c = 0,
-                                             const f2_t post_p = 0)
+                                             const f2_t post_p = 0, HOOK *hook = nullptr)
 {
     using C = typename StorageTraits<S>::C;
     using G = Sweep2DGeom<S, BT, R, V_>;
@@ -591,6 +602,8 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
                 const int i = ib + k;
                 if (CHECK && i >= iend) return true;
                 if (!load_row(i, k, !CHECK || i < nrows, rr[0][k])) return false;
+                if constexpr (HOOK::active)
+                    if (!CHECK || (i >= R && i < ny + R)) hook->row(0, i, rr[0][k]);
 #pragma unroll
                 for (int t = 1; t <= BT; ++t) {
                     const int j = i - t * R;  // level-t row completed now
@@ -635,6 +648,7 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
 #pragma unroll
                         for (int v = 0; v < V; ++v) rr[t][sj][v] = res[v];
                         if (LEVELS && j >= y0 && j < y1) store_row_to(lvl[t], j, res);
+                        if constexpr (HOOK::active) hook->row(t, j, res);
                     } else {
                         store_row(j, res);
                     }
@@ -680,6 +694,8 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
                 if (CHECK && i >= iend) return true;
                 C in_row[V];
                 if (!load_row(i, k, !CHECK || i < nrows, in_row)) return false;
+                if constexpr (HOOK::active)
+                    if (!CHECK || (i >= R && i < ny + R)) hook->row(0, i, in_row);
 #pragma unroll
                 for (int t = 1; t <= BT; ++t) {
                     const int ar = i - (t - 1) * R;  // arriving level-(t-1) row
@@ -733,6 +749,8 @@ __device__ __forceinline__ bool sweep2d_tile(const Tile2D tg, const CUtensorMap 
 #pragma unroll
                         for (int v = 0; v < V; ++v) in_row[v] = out_row[v];
                         if (LEVELS && e >= y0 && e < y1) store_row_to(lvl[t], e, out_row);
+                        if constexpr (HOOK::active)
+                            if (inner) hook->row(t, e, out_row);
                     } else if (!CHECK || (e >= y0 && e < y1)) {
                         store_row(e, out_row);
                     }
