@@ -630,7 +630,11 @@ def run_ours(args, rank, world, local):
     launch_s = ms_step * 1e-3 / passes            # halo copy (~us) included: conservative
     full_passes = T // bt
     traffic = committed_traffic(args.workload, bt, cfg["tile_x"])
+    from paper_2001_01473_gb300 import kernels as K
+    k9 = (ndim == 3 and shape == STAR and dtype == "f32" and post is None
+          and any(r == R and bt in bts for r, bts, _nw, _rw in K.KERNELS_3D_STAR))
     kernel = (f"box1_kernel bT={bt}" if ndim == 3 and shape == BOX and R >= 2
+              else f"star3d_kernel bT={bt} tile_x={cfg['tile_x']}" if k9
               else f"sweep{ndim}d_kernel bT={bt} tile_x={cfg['tile_x']}")
     roofline = sweep_roofline(ndim, shape, R, dtype, post, cells, bt, launch_s, inrun, kernel, traffic)
     roofline["passes_per_step"] = passes
