@@ -829,6 +829,7 @@ def run_batch(args, rank, world, local):
             "unit": "GCell-updates/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
             "config": {"grids": len(grids), "cell_updates_per_step": cells, "items": info["items"],
                        "persistent_ctas": info["ctas"], "class_bt": info["class_bt"],
+                       "class_tile_x": info["class_tile_x"],
                        "recipe": "sides log-uniform [128,4096], star/box R1-2, T U[10,500], seed 3"},
             "roofline": {"bound": roof["bound"], "roof_time_ms": roof["time_s"] * 1e3,
                          "hbm_time_ms": roof["hbm_s"] * 1e3, "alu_time_ms": roof["alu_s"] * 1e3,

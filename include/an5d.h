@@ -346,6 +346,7 @@ typedef struct {
     int64_t items;         /* (grid, x tile, stream block, pass) work items */
     double cell_updates;   /* sum over grids of ny * nx * T */
     int class_bt[4];       /* degree per class: star R1, star R2, box R1, box R2 */
+    int class_tile_x[4];   /* tile width per class in cells (128, or 192 with the class's wide degree) */
 } an5d_batch_info_t;
 
 /* Create a batch plan: copies descs and coefficients, allocates one scratch
@@ -355,9 +356,10 @@ typedef struct {
 an5d_batch_plan *an5d_batch_plan_create(int n, const an5d_grid_desc *descs);
 
 /* Pick each class's degree among the built ones {1,4,8} (radius 1) and
- * {1,2,4} (radius 2) by timing whole runs of the batch (Section 5.3's
- * tuning by measurement; coordinate descent over the classes, at most two
- * sweeps).  an5d_batch_tune runs on temporary zero-filled buffers of every
+ * {1,2,4} (radius 2), and its tile width (128 cells, or 192 cells at the
+ * class's wide degree: 4 for radius 1, 2 for radius 2), by timing whole
+ * runs of the batch (Section 5.3's tuning by measurement; coordinate
+ * descent over the classes, at most two sweeps).  an5d_batch_tune runs on temporary zero-filled buffers of every
  * grid (allocated and freed here); an5d_batch_tune_run on the caller's ins
  * and outs (same contract as an5d_batch_run; outs are overwritten).
  * Synchronous. */
@@ -366,6 +368,14 @@ int an5d_batch_tune_run(an5d_batch_plan *bp, const void *const *ins, void *const
 
 /* Force the degree of each class (class_bt[4], values from the built menu). */
 int an5d_batch_set_degrees(an5d_batch_plan *bp, const int *class_bt);
+
+/* Force the tile width of each class (class_tile_x[4]: 128 or 192 cells).
+ * A width of 192 takes effect while the class runs at its wide degree (4
+ * for radius 1, 2 for radius 2; the remaining T mod bT steps then run at
+ * degree 1 on the same tiles); at other degrees the class uses 128-cell
+ * tiles.  Tiles of every width give the same bits.  AN5D_ERR_UNSUPPORTED
+ * for other widths. */
+int an5d_batch_set_tiles(an5d_batch_plan *bp, const int *class_tile_x);
 
 /* Advance every grid i by its T: outs[i] = S_i^{T_i}(ins[i]).  ins/outs are
  * host arrays of n device pointers to padded FP32 grids (16-byte aligned,

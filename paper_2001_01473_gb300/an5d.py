@@ -76,11 +76,13 @@ class an5d_grid_desc(ctypes.Structure):
 
 class an5d_batch_info_t(ctypes.Structure):
     _fields_ = [("grids", ctypes.c_int), ("ctas", ctypes.c_int), ("items", ctypes.c_int64),
-                ("cell_updates", ctypes.c_double), ("class_bt", ctypes.c_int * 4)]
+                ("cell_updates", ctypes.c_double), ("class_bt", ctypes.c_int * 4),
+                ("class_tile_x", ctypes.c_int * 4)]
 
     def as_dict(self) -> dict:
         return {"grids": self.grids, "ctas": self.ctas, "items": self.items,
-                "cell_updates": self.cell_updates, "class_bt": list(self.class_bt)}
+                "cell_updates": self.cell_updates, "class_bt": list(self.class_bt),
+                "class_tile_x": list(self.class_tile_x)}
 
 
 class an5d_adjoint_batch_info_t(ctypes.Structure):
@@ -166,6 +168,8 @@ def load(path: str = LIB_PATH):
     L.an5d_batch_tune_run.restype = I
     L.an5d_batch_set_degrees.argtypes = [P, P]
     L.an5d_batch_set_degrees.restype = I
+    L.an5d_batch_set_tiles.argtypes = [P, P]
+    L.an5d_batch_set_tiles.restype = I
     L.an5d_batch_run.argtypes = [P, P, P, P]
     L.an5d_batch_run.restype = I
     L.an5d_batch_status.argtypes = [P]
@@ -519,6 +523,11 @@ def an5d_batch_set_degrees(bp: int, class_bt) -> int:
     return _bcheck(load().an5d_batch_set_degrees(bp, ctypes.cast(a, ctypes.c_void_p)))
 
 
+def an5d_batch_set_tiles(bp: int, class_tile_x) -> int:
+    a = (ctypes.c_int * 4)(*[int(x) for x in class_tile_x])
+    return _bcheck(load().an5d_batch_set_tiles(bp, ctypes.cast(a, ctypes.c_void_p)))
+
+
 def an5d_batch_run(bp: int, ins, outs, stream=None) -> int:
     n = len(ins)
     pi = (ctypes.c_void_p * n)(*[_ptr(x) for x in ins])
@@ -559,6 +568,9 @@ class Batch:
 
     def set_degrees(self, class_bt) -> None:
         an5d_batch_set_degrees(self.handle, class_bt)
+
+    def set_tiles(self, class_tile_x) -> None:
+        an5d_batch_set_tiles(self.handle, class_tile_x)
 
     def run(self, ins, outs, stream=None) -> None:
         an5d_batch_run(self.handle, ins, outs, stream)

@@ -36,6 +36,11 @@ __host__ __device__ constexpr int batch_menu(int cls, int i)
     // radius 1: bT 1, 4, 8; radius 2: bT 1, 2, 4 (degree 1 also runs remainders)
     return (cls % 2 == 0) ? (i == 0 ? 1 : (i == 1 ? 4 : 8)) : (i == 0 ? 1 : (i == 1 ? 2 : 4));
 }
+// A wider tile (6 cells per lane, 192 cells) is built for one degree per
+// class (radius 1: bT 4, radius 2: bT 2) and for its remainder degree 1:
+// the level rings of the larger degrees would not fit the kernel's registers.
+__host__ __device__ constexpr int batch_wide_deg(int cls) { return (cls % 2 == 0) ? 4 : 2; }
+constexpr int BATCH_WIDE_V = 6;
 constexpr int BATCH_MAX_N = 25;
 constexpr int BATCH_WARPS = 4;
 
@@ -46,6 +51,7 @@ struct alignas(64) BatchGrid {
     int bt, full, rem, passes;  // degree, full-degree passes, remainder passes, total
     int rdeg[8];                // degrees of the remainder passes (T mod bT split over the menu)
     int lead;                   // bT*R: tiles start this far left of their compute region
+    int v;                      // cells per lane of the grid's tiles (4 or 6)
     int stride, tiles_x, hsn, nsb;
     int counter_base;
     float coeffs[BATCH_MAX_N];
@@ -56,14 +62,16 @@ struct BatchItem {
 };
 
 // Shared memory per warp: the largest ring among the built instantiations.
-template <int SHAPE, int R, int BT> constexpr int batch_ring_bytes()
+template <int SHAPE, int R, int BT, int V = CELLS_PER_LANE> constexpr int batch_ring_bytes()
 {
-    return Sweep2DGeom<float, BT, R>::WARP_BYTES;
+    return Sweep2DGeom<float, BT, R, V>::WARP_BYTES;
 }
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int BATCH_WARP_BYTES =
-    cmax(cmax(batch_ring_bytes<SH_BOX, 1, 8>(), batch_ring_bytes<SH_BOX, 2, 4>()),
-         cmax(batch_ring_bytes<SH_STAR, 1, 8>(), batch_ring_bytes<SH_STAR, 2, 4>()));
+    cmax(cmax(cmax(batch_ring_bytes<SH_BOX, 1, 8>(), batch_ring_bytes<SH_BOX, 2, 4>()),
+              cmax(batch_ring_bytes<SH_STAR, 1, 8>(), batch_ring_bytes<SH_STAR, 2, 4>())),
+         cmax(cmax(batch_ring_bytes<SH_BOX, 1, 4, BATCH_WIDE_V>(), batch_ring_bytes<SH_BOX, 2, 2, BATCH_WIDE_V>()),
+              cmax(batch_ring_bytes<SH_STAR, 1, 4, BATCH_WIDE_V>(), batch_ring_bytes<SH_STAR, 2, 2, BATCH_WIDE_V>())));
 constexpr int BATCH_SMEM = BATCH_WARPS * BATCH_WARP_BYTES + 128;
 
 struct Coeffs25 {
@@ -72,7 +80,7 @@ struct Coeffs25 {
 
 // One pass of one tile with a given stencil and degree; invalidates the
 // ring's mbarriers afterwards so that the next item can initialise its own.
-template <int SHAPE, int R, int BT>
+template <int SHAPE, int R, int BT, int V = CELLS_PER_LANE>
 __device__ __noinline__ bool batch_tile(const Tile2D tg, const CUtensorMap *map, float *dst, int *status,
                                         unsigned char *ring, const float *gc)
 {
@@ -80,11 +88,11 @@ __device__ __noinline__ bool batch_tile(const Tile2D tg, const CUtensorMap *map,
     Coeffs25 cf;
 #pragma unroll
     for (int k = 0; k < N; ++k) cf.c[k] = gc[k];
-    const bool ok = sweep2d_tile<SHAPE, R, BT, float, MODE_PLAIN, false, decltype(cf.c), decltype(cf.c), false, true>(
-        tg, map, dst, status, ring, cf.c, cf.c);
+    const bool ok = sweep2d_tile<SHAPE, R, BT, float, MODE_PLAIN, false, decltype(cf.c), decltype(cf.c), false, true,
+                                 POST_NONE, V>(tg, map, dst, status, ring, cf.c, cf.c);
     __syncwarp();
     if ((threadIdx.x & 31) == 0) {
-        using G = Sweep2DGeom<float, BT, R>;
+        using G = Sweep2DGeom<float, BT, R, V>;
         uint64_t *bars = reinterpret_cast<uint64_t *>(ring + G::D * G::SLOT_BYTES);
         for (int s = 0; s < G::D; ++s)
             asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bars[s])) : "memory");
@@ -94,10 +102,15 @@ __device__ __noinline__ bool batch_tile(const Tile2D tg, const CUtensorMap *map,
 }
 
 template <int SHAPE, int R>
-__device__ __forceinline__ bool batch_dispatch_deg(int deg, const Tile2D &tg, const CUtensorMap *map, float *dst,
-                                                   int *status, unsigned char *ring, const float *gc)
+__device__ __forceinline__ bool batch_dispatch_deg(int deg, int v, const Tile2D &tg, const CUtensorMap *map,
+                                                   float *dst, int *status, unsigned char *ring, const float *gc)
 {
     constexpr int cls = (SHAPE == SH_STAR ? 0 : 2) + (R - 1);
+    if (v == BATCH_WIDE_V) {
+        if (deg == batch_wide_deg(cls))
+            return batch_tile<SHAPE, R, batch_wide_deg(cls), BATCH_WIDE_V>(tg, map, dst, status, ring, gc);
+        return batch_tile<SHAPE, R, 1, BATCH_WIDE_V>(tg, map, dst, status, ring, gc);
+    }
     if (deg == batch_menu(cls, 1)) return batch_tile<SHAPE, R, batch_menu(cls, 1)>(tg, map, dst, status, ring, gc);
     if (deg == batch_menu(cls, 2)) return batch_tile<SHAPE, R, batch_menu(cls, 2)>(tg, map, dst, status, ring, gc);
     return batch_tile<SHAPE, R, 1>(tg, map, dst, status, ring, gc);
@@ -169,10 +182,10 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32)
         const CUtensorMap *map = &g.map[src];
         bool done;
         switch (g.cls) {
-        case 0: done = batch_dispatch_deg<SH_STAR, 1>(deg, tg, map, dst, status, ring, g.coeffs); break;
-        case 1: done = batch_dispatch_deg<SH_STAR, 2>(deg, tg, map, dst, status, ring, g.coeffs); break;
-        case 2: done = batch_dispatch_deg<SH_BOX, 1>(deg, tg, map, dst, status, ring, g.coeffs); break;
-        default: done = batch_dispatch_deg<SH_BOX, 2>(deg, tg, map, dst, status, ring, g.coeffs); break;
+        case 0: done = batch_dispatch_deg<SH_STAR, 1>(deg, g.v, tg, map, dst, status, ring, g.coeffs); break;
+        case 1: done = batch_dispatch_deg<SH_STAR, 2>(deg, g.v, tg, map, dst, status, ring, g.coeffs); break;
+        case 2: done = batch_dispatch_deg<SH_BOX, 1>(deg, g.v, tg, map, dst, status, ring, g.coeffs); break;
+        default: done = batch_dispatch_deg<SH_BOX, 2>(deg, g.v, tg, map, dst, status, ring, g.coeffs); break;
         }
         if (!__all_sync(FULL_MASK, done)) {
             if (lane == 0) atomicExch(abort_flag, 1);
@@ -221,6 +234,7 @@ struct an5d_batch_plan {
     std::vector<std::vector<double>> coeffs;
     std::vector<BatchItem> items;
     int class_bt[BATCH_CLASSES] = {8, 4, 4, 2};
+    int class_v[BATCH_CLASSES] = {4, 4, 4, 4};  // cells per lane of each class's tiles
     int device = 0, sms = 0;
     void *scratch = nullptr;             // all grids' scratch buffers
     std::vector<size_t> scratch_off;
@@ -293,7 +307,8 @@ static void batch_layout(an5d_batch_plan *bp)
             }
         g.passes = g.full + g.rem;
         g.lead = bt * R;
-        g.stride = 32 * CELLS_PER_LANE - 2 * bt * R;
+        g.v = (bp->class_v[g.cls] == BATCH_WIDE_V && bt == batch_wide_deg(g.cls)) ? BATCH_WIDE_V : CELLS_PER_LANE;
+        g.stride = 32 * g.v - 2 * bt * R;
         g.tiles_x = (g.nx + g.stride - 1) / g.stride;
         // stream blocks of at most 256 rows (and at least bT*R rows)
         g.nsb = std::max(1, (g.ny + 255) / 256);
@@ -437,13 +452,31 @@ extern "C" int an5d_batch_set_degrees(an5d_batch_plan *bp, const int *class_bt)
     return batch_upload_layout(bp);
 }
 
+extern "C" int an5d_batch_set_tiles(an5d_batch_plan *bp, const int *class_tile_x)
+{
+    if (!bp || !class_tile_x) return bfail(AN5D_ERR_INVALID_ARG, "NULL argument");
+    for (int c = 0; c < BATCH_CLASSES; ++c)
+        if (class_tile_x[c] != 32 * CELLS_PER_LANE && class_tile_x[c] != 32 * BATCH_WIDE_V)
+            return bfail(AN5D_ERR_UNSUPPORTED, "tile width " + std::to_string(class_tile_x[c]) +
+                                                   " not built (128 or 192 cells)");
+    cudaDeviceSynchronize();
+    for (int c = 0; c < BATCH_CLASSES; ++c) bp->class_v[c] = class_tile_x[c] / 32;
+    batch_layout(bp);
+    return batch_upload_layout(bp);
+}
+
 extern "C" int an5d_batch_info(const an5d_batch_plan *bp, an5d_batch_info_t *info)
 {
     if (!bp || !info) return AN5D_ERR_INVALID_ARG;
     info->grids = bp->n;
     info->items = (int64_t)bp->items.size();
     info->cell_updates = bp->cell_updates;
-    for (int c = 0; c < BATCH_CLASSES; ++c) info->class_bt[c] = bp->class_bt[c];
+    for (int c = 0; c < BATCH_CLASSES; ++c) {
+        info->class_bt[c] = bp->class_bt[c];
+        // the wide tile applies with the class's wide degree only
+        const bool wide = bp->class_v[c] == BATCH_WIDE_V && bp->class_bt[c] == batch_wide_deg(c);
+        info->class_tile_x[c] = 32 * (wide ? BATCH_WIDE_V : CELLS_PER_LANE);
+    }
     info->ctas = bp->ctas;
     return AN5D_OK;
 }
@@ -476,35 +509,53 @@ extern "C" int an5d_batch_tune_run(an5d_batch_plan *bp, const void *const *ins, 
     cudaStream_t st = (cudaStream_t)stream;
     bool present[BATCH_CLASSES] = {false, false, false, false};
     for (int i = 0; i < bp->n; ++i) present[batch_cls(bp->descs[i].shape, bp->descs[i].radius)] = true;
-    int best[BATCH_CLASSES];
-    for (int c = 0; c < BATCH_CLASSES; ++c) best[c] = bp->class_bt[c];
+    int best[BATCH_CLASSES], best_v[BATCH_CLASSES];
+    for (int c = 0; c < BATCH_CLASSES; ++c) {
+        best[c] = bp->class_bt[c];
+        best_v[c] = bp->class_v[c];
+    }
+    auto apply = [&](const int *bt, const int *v) -> int {
+        int tx[BATCH_CLASSES];
+        for (int c = 0; c < BATCH_CLASSES; ++c) tx[c] = 32 * v[c];
+        cudaDeviceSynchronize();
+        for (int c = 0; c < BATCH_CLASSES; ++c) bp->class_v[c] = tx[c] / 32;
+        return an5d_batch_set_degrees(bp, bt);
+    };
+    if (int s = apply(best, best_v)) return s;
     float t_best = 0;
     if (int s = batch_time(bp, ins, outs, st, &t_best)) return s;
-    // coordinate descent over the classes' degrees, timing the whole batch
-    // (the degrees interact through the shared queue, so a class is not tuned
-    // on a grid of its own)
+    // coordinate descent over the classes' (degree, tile width) options,
+    // timing the whole batch (the choices interact through the shared queue,
+    // so a class is not tuned on a grid of its own)
     for (int sweep = 0; sweep < 2; ++sweep) {
         bool changed = false;
         for (int c = 0; c < BATCH_CLASSES; ++c) {
             if (!present[c]) continue;
-            for (int m = 0; m < BATCH_MENU; ++m) {
-                int trial[BATCH_CLASSES];
-                for (int k = 0; k < BATCH_CLASSES; ++k) trial[k] = best[k];
-                trial[c] = batch_menu(c, m);
-                if (trial[c] == best[c]) continue;
-                if (int s = an5d_batch_set_degrees(bp, trial)) return s;
+            for (int m = 0; m <= BATCH_MENU; ++m) {
+                int trial[BATCH_CLASSES], trial_v[BATCH_CLASSES];
+                for (int k = 0; k < BATCH_CLASSES; ++k) trial[k] = best[k], trial_v[k] = best_v[k];
+                if (m < BATCH_MENU) {
+                    trial[c] = batch_menu(c, m);
+                    trial_v[c] = CELLS_PER_LANE;
+                } else {
+                    trial[c] = batch_wide_deg(c);
+                    trial_v[c] = BATCH_WIDE_V;
+                }
+                if (trial[c] == best[c] && trial_v[c] == best_v[c]) continue;
+                if (int s = apply(trial, trial_v)) return s;
                 float t = 0;
                 if (int s = batch_time(bp, ins, outs, st, &t)) return s;
                 if (t < t_best) {
                     t_best = t;
                     best[c] = trial[c];
+                    best_v[c] = trial_v[c];
                     changed = true;
                 }
             }
         }
         if (!changed) break;
     }
-    return an5d_batch_set_degrees(bp, best);
+    return apply(best, best_v);
 }
 
 extern "C" int an5d_batch_tune(an5d_batch_plan *bp, void *stream)

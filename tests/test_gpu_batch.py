@@ -50,6 +50,29 @@ def test_batch_small_vs_oracle(degrees):
         _check_vs_oracle(grids, xs, ys)
 
 
+@pytest.mark.parametrize("tiles", [(192, 192, 192, 192), (192, 128, 128, 192)])
+def test_batch_wide_tiles_vs_oracle(tiles):
+    """192-cell tiles at each class's wide degree (4 for radius 1, 2 for
+    radius 2; the remaining steps at degree 1 on the same tiles) give the
+    oracle's bits; the info reports the width in force per class."""
+    import torch
+    grids = _grids_from(SMALL)
+    with an5d.Batch(grids) as b:
+        b.set_degrees((4, 2, 4, 2))
+        b.set_tiles(tiles)
+        assert b.info()["class_tile_x"] == list(tiles)
+        xs, ys = _inputs(grids)
+        b.run(xs, ys)
+        torch.cuda.synchronize()
+        assert b.status() == 0, an5d.an5d_batch_last_error()
+        _check_vs_oracle(grids, xs, ys)
+        b.set_degrees((8, 4, 1, 1))          # not the wide degrees: 128-cell tiles
+        assert b.info()["class_tile_x"] == [128, 128, 128, 128]
+        with pytest.raises(an5d.An5dError) as e:
+            b.set_tiles((256, 128, 128, 128))
+        assert e.value.status == an5d.AN5D_ERR_UNSUPPORTED
+
+
 def test_batch_graph_replay_and_new_buffers():
     import torch
     grids = _grids_from(SMALL[:10])
