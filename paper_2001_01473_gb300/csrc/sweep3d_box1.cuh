@@ -57,6 +57,47 @@ template <typename S, int R, int NW, int RW_> struct Box1Geom {
     static_assert(RW <= 32, "one TMA row per lane");
 };
 
+// E cells at p (shared memory) into w, with the widest reads the address
+// allows: the row's misalignment is the same for every lane (a tile row keeps
+// the global row's offset), so the choice does not diverge; 16-byte reads at
+// a 16-byte lane stride take a quarter of the wavefronts of 4-byte reads.
+template <typename S, int E> __device__ __forceinline__ void load_window(const S *p, typename StorageTraits<S>::C (&w)[E])
+{
+    const unsigned a = (unsigned)reinterpret_cast<uintptr_t>(p);
+    if constexpr (std::is_same<S, float>::value && E % 4 == 0) {
+        if ((a & 15u) == 0) {
+#pragma unroll
+            for (int i = 0; i < E / 4; ++i) {
+                const float4 q = reinterpret_cast<const float4 *>(p)[i];
+                w[4 * i] = q.x, w[4 * i + 1] = q.y, w[4 * i + 2] = q.z, w[4 * i + 3] = q.w;
+            }
+            return;
+        }
+    }
+    if constexpr (std::is_same<S, float>::value && E % 2 == 0) {
+        if ((a & 7u) == 0) {
+#pragma unroll
+            for (int i = 0; i < E / 2; ++i) {
+                const float2 q = reinterpret_cast<const float2 *>(p)[i];
+                w[2 * i] = q.x, w[2 * i + 1] = q.y;
+            }
+            return;
+        }
+    }
+    if constexpr (std::is_same<S, double>::value && E % 2 == 0) {
+        if ((a & 15u) == 0) {
+#pragma unroll
+            for (int i = 0; i < E / 2; ++i) {
+                const double2 q = reinterpret_cast<const double2 *>(p)[i];
+                w[2 * i] = q.x, w[2 * i + 1] = q.y;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) w[e] = load_c<S>(p[e]);
+}
+
 template <int R, typename S, int NW, int RW_>
 __global__ void __launch_bounds__(NW * 32, 1)
     box1_kernel(const __grid_constant__ CUtensorMap tmap,
@@ -98,8 +139,9 @@ __global__ void __launch_bounds__(NW * 32, 1)
             if (y >= sr0 && y < sr1 && x >= sc0 && x < sc1) store_bits |= 1u << (r * V + v);
         }
 
-    unsigned char *const base = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
+    // aligned by pointer arithmetic on the shared array, so that the compiler
+    // keeps the window reads below in the shared address space
+    unsigned char *const base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
     unsigned char *const ring = base + G::PAD;
     uint64_t *const bars = reinterpret_cast<uint64_t *>(ring + D * G::SLOT_BYTES);
     int *const status = a.status;
@@ -176,8 +218,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
             const int off = (int)((pl + (long)(yb + tr) * px + x0) & long(A - 1));
             const S *src = reinterpret_cast<const S *>(slot + tr * G::ROW_BYTES) + off + lane * V - R;
             C w[V + 2 * R];  // cells x-R .. x+V-1+R of this row
-#pragma unroll
-            for (int e = 0; e < V + 2 * R; ++e) w[e] = load_c<S>(src[e]);
+            load_window<S, V + 2 * R>(src, w);
 #pragma unroll
             for (int d = 0; d < P; ++d) {
                 const int dz = R - d;
