@@ -60,8 +60,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (Sweep2DOccupancy<float, S
     tg.y0 = R + sbk * a.hsn;
     tg.y1 = min(tg.y0 + a.hsn, a.ny + R);
     tg.stall = 0;
-    unsigned char *const smem_al = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
+    unsigned char *const smem_al = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
     sweep2d_tile<SHAPE, R, BT, float, MODE_PLAIN, false, decltype(a.k.c), decltype(a.k.c), true>(
         tg, &tmap, a.dst, a.status, smem_al + warp * G::WARP_BYTES, a.k.c, a.k.c, lv.p);
 }

@@ -307,8 +307,7 @@ __global__ void __launch_bounds__(ADJB_WARPS * 32)
                      int *counters, int *status, int *abort_flag)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *const base = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
+    unsigned char *const base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     unsigned char *const ring = base + warp * ADJB_WARP_BYTES;

@@ -164,8 +164,9 @@ __global__ void __launch_bounds__(NW * 32, 1)
         }
     const bool edge = __syncthreads_or(halo_bits != 0) != 0;
 
-    unsigned char *const base = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
+    // aligned by pointer arithmetic on the shared array, so that the compiler
+    // keeps the staged-row and exchange accesses in the shared address space
+    unsigned char *const base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
     unsigned char *const ring = base;
     C *const xb = reinterpret_cast<C *>(base + D * G::SLOT_BYTES);
     uint64_t *const bars = reinterpret_cast<uint64_t *>(base + D * G::SLOT_BYTES + G::XB_BYTES);
