@@ -807,8 +807,13 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32,
     tg.y0 = R + sbk * a.hsn;
     tg.y1 = min(tg.y0 + a.hsn, a.ny + R);
     tg.stall = a.stall_test && gw == 0;
-    unsigned char *const smem_al = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
+    // Box chains address the rings through a pointer derived from the shared
+    // array by arithmetic (the compiler then keeps their accesses in the
+    // shared address space); star chains through the generic round trip,
+    // which measured faster for them.
+    unsigned char *const smem_al =
+        SHAPE == SH_BOX ? smem + ((128u - (smem_u32(smem) & 127u)) & 127u)
+                        : reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));
     // Boxes of radius 2 and more run the scalar chain: with (2R+1)^2 terms the
     // odd x shifts (scalar fmas on repacked halves) outnumber the paired
     // terms, and the plain chain with constant-bank coefficients measured
