@@ -483,7 +483,9 @@ cudaError_t launch_star3d(const PassDesc &d, cudaStream_t st)
 }
 
 // PART_ = 1 registers the kernel as the narrow last-column kernel of the
-// passes whose main kernel has the same key (same NW and RW: same tile rows).
+// passes whose main kernel has the same key (same NW and RW: same tile rows);
+// with PART_ = 0 and another cells-per-lane count than the default, the
+// kernel is a tile variant of its width.
 template <int R, int BT, int NW, int V_ = CELLS_PER_LANE, int RW_ = 2, int PART_ = 0>
 KernelEntry entry_star3d()
 {
@@ -491,6 +493,8 @@ KernelEntry entry_star3d()
     KernelEntry e;
     e.key = KernelKey{3, SH_STAR, R, DT_F32, BT, POST_NONE};
     e.key.part = PART_;
+    // a main kernel of another width is a tile variant, keyed by its width
+    if (PART_ == 0 && V_ != CELLS_PER_LANE) e.key.tile = G::TX;
     e.launch = &launch_star3d<R, BT, NW, V_, RW_>;
     e.func = reinterpret_cast<const void *>(&star3d_kernel<R, BT, NW, V_, RW_>);
     e.threads = NW * 32;

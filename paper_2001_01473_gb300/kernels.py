@@ -101,6 +101,18 @@ KERNELS_3D_STAR = [
     (4, range(2, 3), 12, 2),
 ]
 
+# Tile variants of the same sweep for the tuner: (radius, bT range, warps per
+# CTA, rows per warp, cells per lane).  A 64 x 64 tile (2 cells per lane, 4
+# rows per warp) holds the same ring registers per thread as the 128 x 32
+# default, loses fewer of its cells to the overlap at bT >= 2 (0.82 of the
+# tile is stored at bT 3 against 0.77), and reads a y neighbour from shared
+# memory for half of its rows instead of all of them, at the cost of twice
+# the x shuffles per cell.  It is keyed by its tile width (64).
+KERNELS_3D_STAR_NARROW = [
+    (1, range(2, 4), 16, 4, 2),
+    (1, range(4, 5), 12, 4, 2),
+]
+
 
 # 3D tile shape per stencil: (cells per lane V, rows per warp RW); the CTA
 # tile is (NW * RW) rows x (32 * V) cells.  128 x 2 by default; the FP64
@@ -178,6 +190,9 @@ def instantiations():
             tv = tail3d(STAR, r, "float", "MODE_PLAIN")
             if tv and tv < 4:
                 yield "sweep3d_star.cuh", f"entry_star3d<{r}, {bt}, {nw}, {tv}, {rw}, 1>()"
+    for r, bts, nw, rw, v in KERNELS_3D_STAR_NARROW:
+        for bt in bts:
+            yield "sweep3d_star.cuh", f"entry_star3d<{r}, {bt}, {nw}, {v}, {rw}, 0>()"
     for r, s, dt, nw, rw in KERNELS_3D_BOX1:
         yield "sweep3d_box1.cuh", f"entry_box1<{r}, {s}, {nw}, {rw}>({dt})"
     for post in POSTS:

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2001_01473_gb300 import an5d, inputs
-from paper_2001_01473_gb300.kernels import KERNELS_3D, KERNELS_3D_BOX1, KERNELS_3D_STAR
+from paper_2001_01473_gb300.kernels import KERNELS_3D, KERNELS_3D_BOX1, KERNELS_3D_STAR, KERNELS_3D_STAR_NARROW
 from _gpu_util import assert_bitwise, coeffs_for, gpu_run, oracle_run
 
 pytestmark = pytest.mark.gpu
@@ -31,6 +31,22 @@ def test_parity_3d_several_tiles_ragged(shape, R, dt, bt):
         ref = oracle_run(3, shape, R, c, dt, dims, u0, T)
         got = gpu_run(3, shape, R, c, dt, dims, u0, T, bT=bt, hsn=7)
         assert_bitwise(got, ref, f"3d shape={shape} R={R} {dt} bT={bt} T={T}")
+
+
+VARIANT_CASES = [(r, 32 * v, bt) for r, bts, _nw, _rw, v in KERNELS_3D_STAR_NARROW for bt in bts]
+
+
+@pytest.mark.parametrize("R,tile,bt", VARIANT_CASES)
+def test_parity_3d_tile_variant(R, tile, bt):
+    # the 64-cell-wide FP32 star tiles: several tiles in x and y with ragged
+    # tails, stream blocks of 5 planes, and a degenerate thin grid
+    c = coeffs_for(3, STAR, R, seed=7)
+    for dims in [(21, 150, 131), (4, 3, 61)]:
+        u0 = inputs.field(dims, R, 2, "f32")
+        for T in sorted({1, bt, bt + 1, 2 * bt + 1}):
+            ref = oracle_run(3, STAR, R, c, "f32", dims, u0, T)
+            got = gpu_run(3, STAR, R, c, "f32", dims, u0, T, bT=bt, hsn=5, tile=tile)
+            assert_bitwise(got, ref, f"3d star R={R} tile={tile} bT={bt} T={T} dims={dims}")
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (1, 5, 300), (40, 1, 1), (3, 40, 7), (9, 33, 129),
@@ -146,6 +162,7 @@ def test_narrow_last_column(shape, R, bt, rest):
     T = 2 * bt + 1
     with an5d.Plan(3, shape, R, c, "f32", dims) as plan:
         plan.set_config(bt, 4)
+        plan.set_tile(0)  # the default 128-cell tile (the narrow column belongs to it)
         cfg = plan.config()
         assert cfg["launches_per_pass"] == (2 if 0 < rest <= ts_narrow else 1), (cfg, rest)
         # 2 halo copies + 3 passes (2 of bT, 1 of 1 step), a narrow launch more where split
@@ -170,6 +187,7 @@ def test_narrow_column_runs_in_a_captured_graph():
     T = 2 * bt + 2
     with an5d.Plan(3, STAR, R, c, "f32", dims) as plan:
         plan.set_config(bt, 5)
+        plan.set_tile(0)  # the default 128-cell tile and its narrow last column
         assert plan.config()["launches_per_pass"] == 2
         x = torch.empty(inputs.padded_shape(dims, R), dtype=torch.float32, device="cuda")
         y = torch.empty_like(x)

@@ -23,10 +23,11 @@ CASES = [
     (2, BOX, 1, "f32c", (70, 260), 9),
     (2, STAR, 3, "f32", (31, 129), 1),     # one pass
     (2, STAR, 1, "f32", (16, 16), 0),      # copy only
-    # 3D: at every degree 1-4 a 136-wide grid is one full 128-cell tile
-    # column plus a remainder that fits the narrow last-column kernel, which
-    # the allocation-free call runs after the main launch on the same stream
-    (3, STAR, 1, "f32", (21, 40, 136), 7),
+    # 3D: at every degree 1-3 of the radius-2 star a 136-wide grid is one
+    # full 128-cell tile column plus a remainder that fits the narrow
+    # last-column kernel, which the allocation-free call runs after the main
+    # launch on the same stream
+    (3, STAR, 2, "f32", (21, 40, 136), 7),
     (3, BOX, 1, "f64", (13, 30, 70), 4),   # 3D box, FP64
 ]
 
