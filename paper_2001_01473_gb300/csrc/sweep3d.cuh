@@ -568,14 +568,18 @@ cudaError_t launch_sweep3d(const PassDesc &d, cudaStream_t st)
 
 // PART_ = 1 registers the kernel as the narrow last-column kernel of the
 // passes whose main kernel has the same key (same NW and RW: same tile rows).
+// TILE_ > 0 registers it as a tile variant keyed by that width (the tuner
+// times it beside the default tile of the same stencil and degree).
 template <int SHAPE, int R, int BT, typename S, int MODE, int NW, int POST = POST_NONE,
-          int V_ = CELLS_PER_LANE, int RW_ = 2, int PART_ = 0>
+          int V_ = CELLS_PER_LANE, int RW_ = 2, int PART_ = 0, int TILE_ = 0>
 KernelEntry entry3d(int dtype)
 {
     using G = Sweep3DGeom<S, SHAPE, BT, R, NW, V_, RW_>;
+    static_assert(TILE_ == 0 || (TILE_ == G::TX && PART_ == 0), "a tile variant is keyed by its own width");
     KernelEntry e;
     e.key = KernelKey{3, SHAPE, R, dtype, BT, POST};
     e.key.part = PART_;
+    e.key.tile = TILE_;
     e.launch = &launch_sweep3d<SHAPE, R, BT, S, MODE, NW, POST, V_, RW_>;
     e.func = reinterpret_cast<const void *>(&sweep3d_kernel<SHAPE, R, BT, S, MODE, NW, POST, V_, RW_>);
     e.threads = NW * 32;

@@ -107,7 +107,9 @@ KERNELS_3D_STAR = [
 # default, loses fewer of its cells to the overlap at bT >= 2 (0.82 of the
 # tile is stored at bT 3 against 0.77), and reads a y neighbour from shared
 # memory for half of its rows instead of all of them, at the cost of twice
-# the x shuffles per cell.  It is keyed by its tile width (64).
+# the x shuffles per cell.  Keyed by the tile width (64).  (Measured and not
+# kept: the radius-2 star at 64 x 48 and 64 x 32 cells, bT 2 and 3, which the
+# tuner did not pick over the default tiles on 512^3.)
 KERNELS_3D_STAR_NARROW = [
     (1, range(2, 4), 16, 4, 2),
     (1, range(4, 5), 12, 4, 2),
@@ -168,6 +170,18 @@ KERNELS_DIV_3D = [
     (BOX, 1, range(1, 2), "double", "DT_F64", 12),
 ]
 
+# Tile variants of the per-level-exchange 3D sweep, timed by the tuner beside
+# the default tile of the same stencil and degree: (shape, radius, bT range,
+# storage, dtype, warps per CTA, cells per lane, rows per warp, division
+# forms).  64 x 64 tiles for the radius-1 box: the same registers per thread
+# as the default 128 x 32 tile and a smaller share of overlap cells at
+# bT >= 2.  (Its division forms were measured and not kept: the tuner kept
+# the default tile for j3d27pt on 512^3.)
+KERNELS_3D_VARIANTS = [
+    (BOX, 1, range(1, 3), "float", "DT_F32", 16, 2, 4, ("POST_NONE",)),
+    (BOX, 1, range(3, 4), "float", "DT_F32", 12, 2, 4, ("POST_NONE",)),
+]
+
 
 def instantiations():
     """Yield (header, entry expression) for every kernel instantiation."""
@@ -195,6 +209,11 @@ def instantiations():
             yield "sweep3d_star.cuh", f"entry_star3d<{r}, {bt}, {nw}, {v}, {rw}, 0>()"
     for r, s, dt, nw, rw in KERNELS_3D_BOX1:
         yield "sweep3d_box1.cuh", f"entry_box1<{r}, {s}, {nw}, {rw}>({dt})"
+    for shape, r, bts, s, dt, nw, v, rw, posts in KERNELS_3D_VARIANTS:
+        for post in posts:
+            for bt in bts:
+                yield "sweep3d.cuh", (f"entry3d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {nw}, {post}, {v}, {rw}, 0, "
+                                      f"{32 * v}>({dt})")
     for post in POSTS:
         for shape, r, bts, s, dt in KERNELS_DIV_2D:
             for bt in bts:

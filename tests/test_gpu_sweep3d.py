@@ -4,7 +4,8 @@ import numpy as np
 import pytest
 
 from paper_2001_01473_gb300 import an5d, inputs
-from paper_2001_01473_gb300.kernels import KERNELS_3D, KERNELS_3D_BOX1, KERNELS_3D_STAR, KERNELS_3D_STAR_NARROW
+from paper_2001_01473_gb300.kernels import (KERNELS_3D, KERNELS_3D_BOX1, KERNELS_3D_STAR, KERNELS_3D_STAR_NARROW,
+                                            KERNELS_3D_VARIANTS)
 from _gpu_util import assert_bitwise, coeffs_for, gpu_run, oracle_run
 
 pytestmark = pytest.mark.gpu
@@ -33,20 +34,22 @@ def test_parity_3d_several_tiles_ragged(shape, R, dt, bt):
         assert_bitwise(got, ref, f"3d shape={shape} R={R} {dt} bT={bt} T={T}")
 
 
-VARIANT_CASES = [(r, 32 * v, bt) for r, bts, _nw, _rw, v in KERNELS_3D_STAR_NARROW for bt in bts]
+VARIANT_CASES = ([(STAR, r, "f32", 32 * v, bt) for r, bts, _nw, _rw, v in KERNELS_3D_STAR_NARROW for bt in bts] +
+                 [(SH[sh], r, DT[dt], 32 * v, bt) for sh, r, bts, _s, dt, _nw, v, _rw, posts in KERNELS_3D_VARIANTS
+                  if "POST_NONE" in posts for bt in bts])
 
 
-@pytest.mark.parametrize("R,tile,bt", VARIANT_CASES)
-def test_parity_3d_tile_variant(R, tile, bt):
-    # the 64-cell-wide FP32 star tiles: several tiles in x and y with ragged
-    # tails, stream blocks of 5 planes, and a degenerate thin grid
-    c = coeffs_for(3, STAR, R, seed=7)
+@pytest.mark.parametrize("shape,R,dt,tile,bt", VARIANT_CASES)
+def test_parity_3d_tile_variant(shape, R, dt, tile, bt):
+    # the 64-cell-wide tiles: several tiles in x and y with ragged tails,
+    # stream blocks of 5 planes, and a degenerate thin grid
+    c = coeffs_for(3, shape, R, seed=7)
     for dims in [(21, 150, 131), (4, 3, 61)]:
-        u0 = inputs.field(dims, R, 2, "f32")
+        u0 = inputs.field(dims, R, 2, dt)
         for T in sorted({1, bt, bt + 1, 2 * bt + 1}):
-            ref = oracle_run(3, STAR, R, c, "f32", dims, u0, T)
-            got = gpu_run(3, STAR, R, c, "f32", dims, u0, T, bT=bt, hsn=5, tile=tile)
-            assert_bitwise(got, ref, f"3d star R={R} tile={tile} bT={bt} T={T} dims={dims}")
+            ref = oracle_run(3, shape, R, c, dt, dims, u0, T)
+            got = gpu_run(3, shape, R, c, dt, dims, u0, T, bT=bt, hsn=5, tile=tile)
+            assert_bitwise(got, ref, f"3d shape={shape} R={R} tile={tile} bT={bt} T={T} dims={dims}")
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (1, 5, 300), (40, 1, 1), (3, 40, 7), (9, 33, 129),
