@@ -216,8 +216,10 @@ int an5d_plan_set_coeffs(an5d_plan *plan, const double *coeffs);
  * rank every built bT and stream-block length of every tile variant with
  * the analytic model, time each variant's top `topk` candidates on the
  * plan's scratch buffers for
- * `T_probe` steps on `stream`, keep the fastest.  Synchronous.  Results
- * are cached per (stencil, dtype, division, dims, device) for the process. */
+ * `T_probe` steps on `stream`, then time up to five more stream-block
+ * lengths around the fastest one's (0.5x to 2x its block count), and keep
+ * the fastest of all.  Synchronous.  Results are cached per (stencil,
+ * dtype, division, dims, device) for the process. */
 int an5d_plan_tune(an5d_plan *plan, int topk, int64_t T_probe, void *stream);
 
 /* Fault injection for tests of the failure path (2D plans): while enabled,

@@ -813,14 +813,15 @@ extern "C" int an5d_plan_tune(an5d_plan *p, int topk, int64_t T_probe, void *str
     double best = -1.0;
     Cand win = cands.empty() ? Cand{save_bt, save_hsn, save_tile, 0.0} : cands[0];
     int status = AN5D_OK;
-    for (const auto &c : cands) {
+    // one warm-up and one timed run of candidate c; false on a run error
+    auto time_cand = [&](const Cand &c) -> bool {
         p->bt = c.bt;
         p->hsn = c.hsn;
         p->tile = c.tile;
         const int64_t T = std::max<int64_t>(T_probe, c.bt);
-        if ((status = run_impl(p, a, b, T, st))) break;   // warm-up
+        if ((status = run_impl(p, a, b, T, st))) return false;   // warm-up
         cudaEventRecord(e0, st);
-        if ((status = run_impl(p, a, b, T, st))) break;
+        if ((status = run_impl(p, a, b, T, st))) return false;
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -829,6 +830,28 @@ extern "C" int an5d_plan_tune(an5d_plan *p, int topk, int64_t T_probe, void *str
         if (g > best) {
             best = g;
             win = c;
+        }
+        return true;
+    };
+    for (const auto &c : cands)
+        if (!time_cand(c)) break;
+    // Refine the winner's stream block by measurement: the model's wave
+    // arithmetic only proposes a few lengths, and the measured rate moves by
+    // several percent between neighbouring ones (lead-in planes against the
+    // fill of the last wave).  Time the block counts around the winner's.
+    if (status == AN5D_OK && !cands.empty()) {
+        const Cand w0 = win;
+        const int64_t slen = p->ndim == 3 ? p->nz : p->ny;
+        const int64_t nsb = (slen + w0.hsn - 1) / w0.hsn;
+        std::vector<int> tried{w0.hsn};
+        for (const auto &c : cands)
+            if (c.bt == w0.bt && c.tile == w0.tile) tried.push_back(c.hsn);
+        for (double f : {0.5, 0.75, 1.25, 1.5, 2.0}) {
+            const int64_t n = std::max<int64_t>(1, std::min<int64_t>(slen, (int64_t)std::llround(nsb * f)));
+            const int h = (int)((slen + n - 1) / n);
+            if (std::find(tried.begin(), tried.end(), h) != tried.end()) continue;
+            tried.push_back(h);
+            if (!time_cand(Cand{w0.bt, h, w0.tile, model_for(p, w0.bt, h)})) break;
         }
     }
     cudaEventDestroy(e0);
