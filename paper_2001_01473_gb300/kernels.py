@@ -120,8 +120,15 @@ KERNELS_3D_STAR_NARROW = [
 # tile is (NW * RW) rows x (32 * V) cells.  128 x 2 by default; the FP64
 # radius-1 star uses 64-cell-wide tiles of 4 rows per warp, which waste
 # fewer overlap cells on 512-wide grids (measured faster there; in FP32 the
-# extra shuffles and row addressing cost more than the overlap saves).
+# extra shuffles and row addressing cost more than the overlap saves).  The
+# FP64 radius-3 star takes 3 rows per warp (24-row tiles instead of 16, of
+# which 2R = 6 rows are overlap): 14.8 against 11.1 GCell/s on 512^3, with
+# the rings still in registers (236 per thread); for radius 4 the same
+# spills, and for the FP32 radius-3 star a 48-row tile (12 warps x 4 rows)
+# spilled and measured slower (224 against 317).
 def geom3d(shape, r, s):
+    if s == "double" and shape == STAR and r == 3:
+        return (4, 3)
     return (2, 4) if (s == "double" and shape == STAR and r == 1) else (4, 2)
 
 
@@ -172,14 +179,17 @@ KERNELS_DIV_3D = [
 
 # Tile variants of the per-level-exchange 3D sweep, timed by the tuner beside
 # the default tile of the same stencil and degree: (shape, radius, bT range,
-# storage, dtype, warps per CTA, cells per lane, rows per warp, division
-# forms).  64 x 64 tiles for the radius-1 box: the same registers per thread
+# storage, mode, dtype, warps per CTA, cells per lane, rows per warp,
+# division forms).  64 x 64 tiles for the radius-1 box: the same registers per thread
 # as the default 128 x 32 tile and a smaller share of overlap cells at
 # bT >= 2.  (Its division forms were measured and not kept: the tuner kept
 # the default tile for j3d27pt on 512^3.)
 KERNELS_3D_VARIANTS = [
-    (BOX, 1, range(1, 3), "float", "DT_F32", 16, 2, 4, ("POST_NONE",)),
-    (BOX, 1, range(3, 4), "float", "DT_F32", 12, 2, 4, ("POST_NONE",)),
+    (BOX, 1, range(1, 3), "float", "MODE_PLAIN", "DT_F32", 16, 2, 4, ("POST_NONE",)),
+    (BOX, 1, range(3, 4), "float", "MODE_PLAIN", "DT_F32", 12, 2, 4, ("POST_NONE",)),
+    (STAR, 2, range(1, 2), "double", "MODE_PLAIN", "DT_F64", 12, 2, 4, ("POST_NONE",)),
+    (STAR, 1, range(1, 4), "float", "MODE_DOT2", "DT_F32C", 16, 2, 4, ("POST_NONE",)),
+    (STAR, 1, range(1, 4), "__half", "MODE_PLAIN", "DT_F16S", 16, 2, 4, ("POST_NONE",)),
 ]
 
 
@@ -209,10 +219,10 @@ def instantiations():
             yield "sweep3d_star.cuh", f"entry_star3d<{r}, {bt}, {nw}, {v}, {rw}, 0>()"
     for r, s, dt, nw, rw in KERNELS_3D_BOX1:
         yield "sweep3d_box1.cuh", f"entry_box1<{r}, {s}, {nw}, {rw}>({dt})"
-    for shape, r, bts, s, dt, nw, v, rw, posts in KERNELS_3D_VARIANTS:
+    for shape, r, bts, s, mode, dt, nw, v, rw, posts in KERNELS_3D_VARIANTS:
         for post in posts:
             for bt in bts:
-                yield "sweep3d.cuh", (f"entry3d<{shape}, {r}, {bt}, {s}, MODE_PLAIN, {nw}, {post}, {v}, {rw}, 0, "
+                yield "sweep3d.cuh", (f"entry3d<{shape}, {r}, {bt}, {s}, {mode}, {nw}, {post}, {v}, {rw}, 0, "
                                       f"{32 * v}>({dt})")
     for post in POSTS:
         for shape, r, bts, s, dt in KERNELS_DIV_2D:

@@ -47,7 +47,7 @@ def _oracle(ndim, shape, R, c, dt, dims, u0, T, post):
 
 
 VARIANT_CASES = [(SH[sh], r, DT[dt], 32 * v, bt, {"POST_DIV": "div", "POST_MUL": "rcp"}[post])
-                 for sh, r, bts, _s, dt, _nw, v, _rw, posts in KERNELS_3D_VARIANTS
+                 for sh, r, bts, _s, _m, dt, _nw, v, _rw, posts in KERNELS_3D_VARIANTS
                  for post in posts if post != "POST_NONE" for bt in bts]
 
 

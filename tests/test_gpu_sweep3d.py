@@ -35,7 +35,7 @@ def test_parity_3d_several_tiles_ragged(shape, R, dt, bt):
 
 
 VARIANT_CASES = ([(STAR, r, "f32", 32 * v, bt) for r, bts, _nw, _rw, v in KERNELS_3D_STAR_NARROW for bt in bts] +
-                 [(SH[sh], r, DT[dt], 32 * v, bt) for sh, r, bts, _s, dt, _nw, v, _rw, posts in KERNELS_3D_VARIANTS
+                 [(SH[sh], r, DT[dt], 32 * v, bt) for sh, r, bts, _s, _m, dt, _nw, v, _rw, posts in KERNELS_3D_VARIANTS
                   if "POST_NONE" in posts for bt in bts])
 
 
