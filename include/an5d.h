@@ -266,7 +266,7 @@ int an5d_run_noalloc(int ndim, an5d_shape shape, int radius, const double *coeff
                      void *stream);
 
 /* Error norms of a run against an FP64 reference, over the interior of a
- * padded grid.  The precision forms are judged against an FP64 evaluation
+ * padded grid.  The precision forms are measured against an FP64 evaluation
  * of the same sweep; FP64 arithmetic on the GPU is otherwise used only by
  * the FP64 plain method.  (No counterpart in the paper, which reports no
  * accuracy figures.)

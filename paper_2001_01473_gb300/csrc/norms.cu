@@ -1,6 +1,6 @@
 // norms.cu -- FP64 error norms of a run against an FP64 reference grid.
 //
-// The precision forms (binary16 storage, Dot2-compensated FP32) are judged
+// The precision forms (binary16 storage, Dot2-compensated FP32) are measured
 // by their distance from an FP64 evaluation of the same sweep: the maximum
 // absolute difference and the L2 norms over the interior.  Sums run in FP64
 // over a fixed partition (1024 blocks, fixed tree inside a block, one
