@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_2001_01473_gb300 import an5d, inputs
-from paper_2001_01473_gb300.kernels import KERNELS_3D_VARIANTS, KERNELS_DIV_2D, KERNELS_DIV_3D
+from paper_2001_01473_gb300.kernels import KERNELS_DIV_2D, KERNELS_DIV_3D
 from _gpu_util import assert_bitwise, gpu_run
 
 pytestmark = pytest.mark.gpu
@@ -44,26 +44,6 @@ def _oracle(ndim, shape, R, c, dt, dims, u0, T, post):
     t = np.float32 if dt == "f32" else np.float64
     p = oracle.POST_DIV if post == "div" else oracle.POST_MUL_RCP
     return oracle.run_div(dt, ndim, shape, R, np.asarray(c).astype(t), DIVISOR, p, dims, u0, T)
-
-
-VARIANT_CASES = [(SH[sh], r, DT[dt], 32 * v, bt, {"POST_DIV": "div", "POST_MUL": "rcp"}[post])
-                 for sh, r, bts, _s, _m, dt, _nw, v, _rw, posts in KERNELS_3D_VARIANTS
-                 for post in posts if post != "POST_NONE" for bt in bts]
-
-
-@pytest.mark.parametrize("shape,R,dt,tile,bt,post", VARIANT_CASES)
-def test_division_parity_3d_tile_variant(shape, R, dt, tile, bt, post):
-    dims = (19, 150, 131)          # several 64 x 64 tiles with ragged tails
-    c = _coeffs(3, shape, R)
-    u0 = inputs.field(dims, R, 4, dt)
-    plan = an5d.Plan(3, shape, R, c, dt, dims, divisor=DIVISOR, post=post)
-    try:
-        for T in sorted({1, bt, bt + 1, 2 * bt + 1}):
-            ref = _oracle(3, shape, R, c, dt, dims, u0, T, post)
-            got = gpu_run(3, shape, R, c, dt, dims, u0, T, bT=bt, hsn=5, plan=plan, tile=tile)
-            assert_bitwise(got, ref, f"3d tile={tile} {post} bT={bt} T={T}")
-    finally:
-        plan.close()
 
 
 @pytest.mark.parametrize("ndim,shape,R,dt,bt,post", _cases())
