@@ -192,11 +192,14 @@ int an5d_plan_set_config(an5d_plan *plan, int bT, int hsn);
 int64_t an5d_plan_launches(const an5d_plan *plan, int64_t T);
 
 /* Select the sweep kernel's tile variant: 0 = the default width (128 cells
- * along x in 2D), else a tile width along x for which a variant is built
+ * along x), else a tile width along x for which a variant is built
  * (2D FP32: 192 cells, 6 per lane, for the radius-1 star at bT 4-6, also in
  * both division forms, the radius-2 star at bT 2-3, the radius-3 star at
  * bT 2 and the radius-1 box at bT 3-5: less overlap per tile at a lower
- * degree).  Keeps bT and hsn; a remainder pass whose
+ * degree; 3D: 64 cells, 2 per lane, on 4-row warps, for the FP32 radius-1
+ * star at bT 2-4, the FP32 radius-1 box at bT 1-3, the Dot2 and binary16
+ * radius-1 stars at bT 1-3 and the FP64 radius-2 star at bT 1: taller tiles
+ * with less overlap in y).  Keeps bT and hsn; a remainder pass whose
  * degree the variant does not build runs on the default kernel.  Returns
  * AN5D_ERR_UNSUPPORTED if no variant of that width exists for the plan's
  * stencil and current bT.  cfg.tile_x reports the width in use. */
