@@ -58,3 +58,29 @@ def test_sweep_roofline_alu_bound_fp64(monkeypatch):
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert math.isclose(r["peak"], 1.057)
     assert math.isclose(r["achieved"], cells * 13 / 0.01 / 1e12)
+
+
+def test_batch_roof_one_grid(monkeypatch):
+    monkeypatch.setattr(bench, "load_measured_peaks", lambda: ({"hbm_gbs": 8000.0}, "measured"))
+    # star R1, 1000 x 2000 cells, T = 23 at degree 4: 5 passes of 4 and the
+    # remaining 3 steps at degree 1 (the menu 8 / 4 / 1 below 4): 8 passes
+    g = (STAR, 1, None, 1000, 2000, 23)
+    r = bench.batch_roof([g], [4, 2, 1, 1])
+    assert math.isclose(r["hbm_s"], 8 * 1000 * 2000 * 8.0 / 8000e9)
+    alu = 152 * 128 * 2 * 2070e6
+    assert math.isclose(r["alu_s"], 1000 * 2000 * 23 * 9 / alu)
+    assert math.isclose(r["time_s"], max(r["hbm_s"], r["alu_s"]))
+
+
+def test_adjoint_roof_one_grid(monkeypatch):
+    monkeypatch.setattr(bench, "load_measured_peaks", lambda: ({"hbm_gbs": 8000.0}, "measured"))
+    # box R2 (n = 25, nb = 2), T = 5: M = 3 blocks of 2, 2, 1 steps.
+    # bytes per cell: 2 forward passes x 8; blocks of 2: recompute 4 + 4, transposed 8 + 8;
+    # the block of 1: transposed 8 + 4
+    g = (BOX, 2, None, 300, 400, 5)
+    r = bench.adjoint_roof([g])
+    byt = 2 * 8 + 2 * ((4 + 4) + (8 + 8)) + (8 + 4)
+    assert math.isclose(r["hbm_s"], 300 * 400 * byt / 8000e9)
+    n = 25
+    fl = (2 * n - 1) * 2 * 2 + 2 * (2 * n - 1) * 1 + 5 * (2 * n - 1 + 2 * n)
+    assert math.isclose(r["alu_s"], 300 * 400 * fl / (152 * 128 * 2 * 2070e6))
