@@ -252,6 +252,27 @@ def barrier(dist, device=None):
 # ---------------------------------------------------------------------------
 # Clock sampling during the timed region.
 
+def summarize_clocks(rows) -> dict:
+    """Summary of nvidia-smi samples taken during the timed region (rows of the
+    ClockSampler fields as strings): median and maximum SM clock, the largest
+    power draw, and every throttle reason seen active in any sample."""
+    def num(s):
+        try:
+            return float(s)
+        except ValueError:
+            return float("nan")
+    sm = [num(r[1]) for r in rows]
+    mx = [num(r[2]) for r in rows]
+    pw = [num(r[3]) for r in rows]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4)
+                      if r[5 + i].lower() in ("active", "1", "yes")})
+    loaded = [s for s, p in zip(sm, pw) if p == p] or sm
+    return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx),
+            "power_w_max": max(p for p in pw if p == p) if any(p == p for p in pw) else None,
+            "samples": len(rows), "reasons": reasons}
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -291,22 +312,7 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-
-        def num(s):
-            try:
-                return float(s)
-            except ValueError:
-                return float("nan")
-        sm = [num(r[1]) for r in rows]
-        mx = [num(r[2]) for r in rows]
-        pw = [num(r[3]) for r in rows]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4)
-                          if r[5 + i].lower() in ("active", "1", "yes")})
-        loaded = [s for s, p in zip(sm, pw) if p == p] or sm
-        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx),
-                "power_w_max": max(p for p in pw if p == p) if any(p == p for p in pw) else None,
-                "samples": len(rows), "reasons": reasons}
+        return summarize_clocks(rows)
 
 
 # ---------------------------------------------------------------------------

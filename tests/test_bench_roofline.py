@@ -84,3 +84,17 @@ def test_adjoint_roof_one_grid(monkeypatch):
     n = 25
     fl = (2 * n - 1) * 2 * 2 + 2 * (2 * n - 1) * 1 + 5 * (2 * n - 1 + 2 * n)
     assert math.isclose(r["alu_s"], 300 * 400 * fl / (152 * 128 * 2 * 2070e6))
+
+
+def test_clock_summary():
+    # index, sm, max sm, power, active mask, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+    rows = [["0", "2070", "2070", "700.5", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+            ["0", "1980", "2070", "1401.0", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+            ["0", "2070", "2070", "[N/A]", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+            ["0", "2040", "2070", "900.0", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"]]
+    c = bench.summarize_clocks(rows)
+    assert c["sm_mhz"] == 2040.0          # median of the three samples with a power reading
+    assert c["sm_max_mhz"] == 2070.0 and c["power_w_max"] == 1401.0 and c["samples"] == 4
+    assert c["reasons"] == ["sw_power_cap"]
+    rows[0][5] = "Active"
+    assert bench.summarize_clocks(rows)["reasons"] == ["hw_slowdown", "sw_power_cap"]
